@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Throughput of the SGM stereo path on GB300, in MDE/s (million disparity
+estimates W*H*D per second).
+
+One step = the whole path on one stereo pair already resident in HBM:
+census + Hamming cost, path aggregation, WTA + right WTA + LR check, median,
+U-/V-maps.  The workload is the KITTI-shaped pair (1242x375, D=128, 9x7
+census, 8 paths, P1=8, P2=96, LR tolerance 1, 3x3 median) on a seeded
+synthetic scene.  L2 is flushed (256 MiB write) between timed steps; each step
+is timed with CUDA events on the launching stream and the flush is outside the
+events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own pair (independent replicas, weak
+scaling); rank 0 prints one JSON line.  ``--impl reference`` times the CPU
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1807_06271_gb300 import scenes  # noqa: E402
+
+WORKLOAD_INDEX = {"pair-320x240-d64-census5x5-4path": 0, "kitti-1242x375-d128-census9x7-8path": 1,
+                  "hd-1280x720-d128-census5x5-4path-uv": 2, "paper-640x360-d60-census5x5-stream4": 5}
+FLUSH_BYTES = 256 << 20
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+# ---------------------------------------------------------------------------
+# host-side helpers (also exercised by the CPU multi-process tests)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(workload_index: int, rank: int) -> int:
+    """Each rank works on its own pair: seed 1807 + workload index + pair index."""
+    return scenes.workload_seed(workload_index, rank)
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    return units_per_rank * world / seconds_max
+
+
+def workload_ops(w) -> dict:
+    """Algorithmic integer operations per disparity estimate for the
+    aggregation kernel: per enabled path 3 min + 2 add + 1 sub + 1 running
+    min = 7; the Hamming cost once per estimate: XOR + POPC for codes of up to
+    32 bits (2), two of each plus an add for 64-bit codes (5)."""
+    npaths = bin(w.path_mask).count("1")
+    nbits = w.census_w * w.census_h - 1
+    cost = 2 if nbits <= 32 else 5
+    return {"per_path": 7, "paths": npaths, "cost": cost, "per_de": 7 * npaths + cost}
+
+
+def int_peak_tops(sm_count=152, int_lanes_per_sm=128, mhz=2070.0) -> float:
+    """32-bit integer add/min/logic issue peak: SMs x INT32 lanes x clock."""
+    return sm_count * int_lanes_per_sm * mhz * 1e6 / 1e12
+
+
+def kernel_source_digest(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str, digest: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; None otherwise."""
+    path = os.path.join(PROFILE_DIR, f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_d = re.search(r"source-digest:\s*([0-9a-f]+)", text)
+    m_t = re.search(r"dram-bytes-per-launch:\s*([0-9.eE+]+)", text)
+    if not m_d or not m_t or m_d.group(1) != digest:
+        return None
+    return float(m_t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.perf_counter())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        t0, t1 = (self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else (0, 1e30)
+        inside = [s for t, s in self.samples if t0 <= t <= t1 + 0.06] or [s for _, s in self.samples]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in inside:
+            f = [x.strip() for x in s.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle arm
+# ---------------------------------------------------------------------------
+
+def oracle_band(scene, w, rows):
+    """A row band of the workload's pair (the first ``rows`` rows)."""
+    return scene.left[:rows].copy(), scene.right[:rows].copy()
+
+
+def time_oracle(w, scene, rows, reps):
+    import oracle
+    left, right = oracle_band(scene, w, rows)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.sgm(left, right, w.D, w.census_w, w.census_h, w.path_mask, w.P1, w.P2, w.lr_tol,
+                   w.median_k, uv=w.uv)
+    dt = time.perf_counter() - t0
+    return dt, w.W * rows * w.D * reps
+
+
+def run_reference(args, w, windex):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    scene = scenes.scene_for(w, rank_seed(windex, 0))
+    # Size each step's sample (a band of rows of the pair) so that warm-up plus
+    # the timed steps take about two minutes of host time in total.
+    probe_rows = min(w.H, 16)
+    t_probe, _ = time_oracle(w, scene, probe_rows, 1)
+    per_row = t_probe / probe_rows
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows = int(min(w.H, max(8, budget / max(per_row, 1e-9))))
+    for _ in range(args.warmup):
+        time_oracle(w, scene, rows, 1)
+    dt, de = time_oracle(w, scene, rows, args.steps)
+    value = de / dt / 1e6
+    sample = (f"first {rows} of {w.H} rows of the {w.W}x{w.H} pair per step (all paths, WTA, LR, "
+              f"median, U/V), single thread")
+    line = {
+        "impl": "reference", "metric": "MDE/s", "value": value, "unit": "MDE/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "W": w.W, "H": w.H, "D": w.D},
+        "cpu_baseline": {"value": value, "unit": "MDE/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the CUDA arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, w, windex):
+    import numpy as np
+    import torch
+
+    from paper_1807_06271_gb300 import sgm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    scene = scenes.scene_for(w, rank_seed(windex, rank))
+    params = sgm.SgmParams(census_w=w.census_w, census_h=w.census_h, path_mask=w.path_mask,
+                           P1=w.P1, P2=w.P2, lr_tolerance=w.lr_tol, median_k=w.median_k)
+    h = sgm.Handle(w.W, w.H, w.D, params)
+    stream = torch.cuda.current_stream()
+    left = torch.from_numpy(scene.left).cuda()
+    right = torch.from_numpy(scene.right).cuda()
+    disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
+    umap = torch.empty((w.D, w.W), dtype=torch.int16, device="cuda")
+    vmap = torch.empty((w.H, w.D), dtype=torch.int16, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        h.compute(left, right, disp, stream)
+        if w.uv:
+            h.uvmap(disp, umap, vmap, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.2)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sgm.sgm_set_timing(h, True)
+    sgm.sgm_get_stage_times(h)  # reset
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.mark()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict L2 between steps (outside the timed events)
+        starts[i].record(stream)
+        step()
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    sampler.mark()
+    if world > 1:
+        torch.distributed.barrier()
+    stage = sgm.sgm_get_stage_times(h)
+    sgm.sgm_set_timing(h, False)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    total_s = sum(step_ms) / 1e3
+    total_s_max = reduce_max(total_s, world)
+    de = w.de_per_frame
+    value = whole_job_rate(de * args.steps, world, total_s_max) / 1e6
+    ms_per_step = total_s_max / args.steps * 1e3
+
+    # dominant kernel and its roofline
+    dom = max((k for k in stage if stage[k][1] > 0), key=lambda k: stage[k][0])
+    dom_ms = stage[dom][0] / max(stage[dom][1], 1)
+    ops = workload_ops(w)
+    mhz = clocks.get("sm_mhz") or 2070.0
+    lanes = 128  # INT32 lanes per SM on GB300 (unified FP32/INT32 datapath)
+    peak = int_peak_tops(152, lanes, 2070.0)
+    achieved = ops["per_de"] * de / (stage["aggregate"][0] / max(stage["aggregate"][1], 1) / 1e3) / 1e12
+    digest = kernel_source_digest(["paper_1807_06271_gb300/csrc/aggregate.cu",
+                                   "paper_1807_06271_gb300/csrc/sgm_internal.cuh"])
+    traffic = profiled_traffic("aggregate", w.name, digest)
+    roofline = {"bound": "alu", "kernel": "aggregate", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
+                "ops_per_de": ops["per_de"], "peak_basis": f"152 SMs x {lanes} INT32 lanes x 2070 MHz",
+                "of": "derived"}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    e2e_steps = max(3, min(args.steps, 200))
+    hl = torch.from_numpy(scene.left).pin_memory()
+    hr = torch.from_numpy(scene.right).pin_memory()
+    hd = torch.empty((w.H, w.W), dtype=torch.uint8).pin_memory()
+    hu = torch.empty((w.D, w.W), dtype=torch.int16).pin_memory() if w.uv else None
+    hv = torch.empty((w.H, w.D), dtype=torch.int16).pin_memory() if w.uv else None
+    for _ in range(2):
+        sgm.sgm_compute_host(h, hl, hr, hd, hu, hv, stream)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sgm.sgm_compute_host(h, hl, hr, hd, hu, hv, stream)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e = {"value": whole_job_rate(de * e2e_steps, world, e2e_s) / 1e6, "unit": "MDE/s",
+           "h2d_bytes_per_step": 2 * w.W * w.H,
+           "d2h_bytes_per_step": w.W * w.H + (2 * w.D * w.W + 2 * w.H * w.D if w.uv else 0),
+           "steps": e2e_steps, "api": "sgm_compute_host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = w.H
+        reps = args.cpu_frames
+        dt, de_cpu = time_oracle(w, scene, rows, reps)
+        cpu = {"value": de_cpu / dt / 1e6, "unit": "MDE/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} full {w.W}x{w.H} pair(s), single thread, {dt:.1f} s"}
+
+    launches_per_step = 4 + (2 if w.uv else 0)
+    if rank == 0:
+        line = {
+            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": w.name, "W": w.W, "H": w.H, "D": w.D,
+                       "census": f"{w.census_w}x{w.census_h}", "path_mask": w.path_mask,
+                       "P1": w.P1, "P2": w.P2, "lr_tol": w.lr_tol, "median_k": w.median_k,
+                       "uv_maps": w.uv, "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "fps": 1e3 / ms_per_step * world,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps,
+            "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stage.items() if v[1]},
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="kitti-1242x375-d128-census9x7-8path",
+                    choices=sorted(WORKLOAD_INDEX))
+    ap.add_argument("--cpu-frames", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    w = scenes.WORKLOADS[args.workload]
+    windex = WORKLOAD_INDEX[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, windex)
+    return run_ours(args, w, windex)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

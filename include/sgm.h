@@ -1,0 +1,155 @@
+/*
+ * libsgm — semi-global-matching stereo and U-/V-disparity maps on GB300 (sm_103a).
+ *
+ * Method: Ruf, Monka, Kollmann, Grinberg, "Real-time on-board obstacle
+ * avoidance for UAVs based on embedded stereo vision" (ISPRS TC I, 2018),
+ * Sec. 3.1 (disparity estimation) and Sec. 3.2 (U-/V-maps).
+ *
+ * Conventions shared by every entry point
+ *   - Images are 8-bit grey, rectified, row-major.  A left/right image row is
+ *     `row_pitch` bytes apart (sgm_params; 0 means W).  Every other array is
+ *     dense row-major with no padding.
+ *   - Disparities are 8-bit; 0xFF (SGM_INVALID) marks a pixel removed by the
+ *     left-right check.  d runs over [0, D).
+ *   - "device" pointers are CUDA global-memory pointers on the handle's device
+ *     (for example torch tensor data pointers); "host" pointers are ordinary
+ *     (preferably pinned) CPU memory.  The caller owns every pointer it passes;
+ *     the handle owns its scratch memory and keeps it between calls.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device-pointer calls are asynchronous: results are valid once the stream
+ *     has been synchronised.  Calls on one handle must not overlap in time on
+ *     different streams (they share the handle's scratch).
+ *   - Every call returns an SGM_* status; nothing throws across the ABI.
+ *     Arguments are validated on the host before any work is queued.
+ */
+#ifndef SGM_H
+#define SGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SGM_OK 0
+#define SGM_ERR_INVALID_ARG 1 /* null/inconsistent argument                       */
+#define SGM_ERR_UNSUPPORTED 2 /* valid but outside what the kernels implement     */
+#define SGM_ERR_OOM 3         /* device or pinned-host allocation failed          */
+#define SGM_ERR_CUDA 4        /* a CUDA runtime call or kernel launch failed      */
+#define SGM_ERR_TIMEOUT 5     /* a bounded device-side wait gave up               */
+
+#define SGM_INVALID 0xFF
+
+/* Path sets (bit r enables direction r).  Directions, as (dx, dy) steps from a
+ * pixel's predecessor to the pixel:
+ *   0 (1,0) left->right      1 (-1,0) right->left
+ *   2 (0,1) top->bottom      3 (0,-1) bottom->top
+ *   4 (1,1) TL->BR           5 (-1,-1) BR->TL
+ *   6 (-1,1) TR->BL          7 (1,-1) BL->TR                                    */
+#define SGM_PATHS_4 0x0F       /* horizontal and vertical, both ways                 */
+#define SGM_PATHS_8 0xFF       /* all eight (Sec. 3.1.3, Fig. 3a)                    */
+#define SGM_PATHS_STREAM4 0x55 /* 0, 45, 90, 135 degrees: the paper's streaming set
+                                  (Sec. 3.1.3, Fig. 2 and Fig. 3b)                   */
+
+typedef struct sgm_handle_s *sgm_handle;
+
+typedef struct sgm_params {
+    int census_w, census_h; /* census window, odd, census_w*census_h-1 <= 64 bits
+                               (Sec. 3.1.2; 5x5 in Sec. 4.1)                         */
+    int path_mask;          /* SGM_PATHS_* or any non-empty subset of 0xFF          */
+    int P1, P2;             /* penalties of Eq. 2, 0 <= P1 <= P2,
+                               census bits + P2 <= 255                              */
+    int lr_tolerance;       /* Sec. 3.1.4; < 0 switches the check off                */
+    int median_k;           /* Sec. 3.1.5; 0 or 1 = off, else odd, <= 7             */
+    int row_pitch;          /* bytes between image rows; 0 = W                       */
+} sgm_params;
+
+/* Create a handle for W x H images and D disparities (1 <= D <= 255) and
+ * allocate all scratch memory on the current CUDA device.  Out of memory ->
+ * SGM_ERR_OOM; unsupported parameters -> SGM_ERR_UNSUPPORTED; *out stays NULL
+ * on failure.  The handle is bound to the device current at creation. */
+int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out);
+
+/* Free the handle and its scratch (synchronises the device first). */
+int sgm_destroy(sgm_handle h);
+
+/* Dense disparity of one rectified pair (Sec. 3.1): census transform and
+ * Hamming cost (Sec. 3.1.2, Eq. 1), aggregation along the enabled paths with
+ * P1/P2 (Sec. 3.1.3, Eq. 2), winner-takes-all, right disparity from the same
+ * aggregated volume and left-right check (Sec. 3.1.4), k x k median
+ * (Sec. 3.1.5).  left/right: device, H rows of row_pitch bytes.  disp: device,
+ * H x W bytes, SGM_INVALID where the LR check failed. */
+int sgm_compute(sgm_handle h, const uint8_t *left, const uint8_t *right,
+                uint8_t *disp, void *stream);
+
+/* U-map and V-map of a disparity map (Sec. 3.2): umap[d*W + x] counts the
+ * pixels of column x with disparity d (D x W); vmap[y*D + d] counts the pixels
+ * of row y with disparity d (H x D).  SGM_INVALID pixels are not counted.
+ * disp, umap, vmap: device.  Every output element is written. */
+int uvmap_compute(sgm_handle h, const uint8_t *disp, uint16_t *umap,
+                  uint16_t *vmap, void *stream);
+
+/* sgm_compute followed by uvmap_compute with HOST buffers: copies left/right
+ * (H x W each, dense) to handle-owned device buffers, runs both, copies disp
+ * (H x W) and, when non-NULL, umap (D x W) and vmap (H x D) back, and waits
+ * for the stream.  Pinned host memory makes the copies asynchronous. */
+int sgm_compute_host(sgm_handle h, const uint8_t *left, const uint8_t *right,
+                     uint8_t *disp, uint16_t *umap, uint16_t *vmap, void *stream);
+
+/* Many pairs in one go (the method of Sec. 3.1 per pair): n handles (each
+ * with its own size and parameters), device pointers left[i], right[i],
+ * disp[i] and optional umap[i]/vmap[i] (NULL = skip maps for pair i).  The
+ * pairs run concurrently on internal streams forked from and joined back to
+ * `stream`.  Handles must be distinct. */
+int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
+                      const uint8_t *const *right, uint8_t *const *disp,
+                      uint16_t *const *umap, uint16_t *const *vmap, void *stream);
+
+/* Short English text for a status code (static storage). */
+const char *sgm_status_string(int status);
+
+/* Sizes the handle was created with; any pointer may be NULL. */
+int sgm_get_shape(sgm_handle h, int *W, int *H, int *D, int *census_bits);
+
+/* ---- per-stage parity access (same kernels as sgm_compute) --------------- */
+
+/* Census codes (Sec. 3.1.2), one uint64 per pixel, H x W each (device). */
+int sgm_debug_census(sgm_handle h, const uint8_t *left, const uint8_t *right,
+                     uint64_t *codes_left, uint64_t *codes_right, void *stream);
+
+/* Aggregated cost L_r of direction r alone (Eq. 2), H x W x D bytes (device),
+ * d fastest.  r must be enabled in the handle's path mask. */
+int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *right,
+                   uint8_t *L, void *stream);
+
+/* Sum over the enabled paths S = C_aggr (Sec. 3.1.3), H x W x D uint16 (device). */
+int sgm_debug_sum(sgm_handle h, const uint8_t *left, const uint8_t *right,
+                  uint16_t *S, void *stream);
+
+/* Left WTA, right WTA and the map after the LR check, before the median
+ * (Sec. 3.1.3-3.1.4), H x W bytes each (device); any may be NULL. */
+int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right,
+                  uint8_t *disp_left, uint8_t *disp_right, uint8_t *disp_lr,
+                  void *stream);
+
+/* ---- stage timing (CUDA events on the caller's stream) ------------------- */
+
+/* Record a start/stop event pair around every kernel of later calls. */
+int sgm_set_timing(sgm_handle h, int enable);
+
+/* Wait for the recorded work, then return for each stage i < n the summed
+ * kernel time in ms (ms[i]) and the number of launches (count[i]) since the
+ * previous read, and reset.  Either array may be NULL.  *n_stages receives
+ * the number of stages. */
+int sgm_get_stage_times(sgm_handle h, float *ms, int *count, int n, int *n_stages);
+
+/* Name of stage i ("census", "aggregate", ...), NULL when out of range. */
+const char *sgm_stage_name(int i);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGM_H */

@@ -1,0 +1,477 @@
+// The C ABI of libsgm: handle life cycle, argument checks, scratch ownership,
+// the stage sequence of one pair and CUDA-event stage timing.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "sgm_internal.cuh"
+
+using namespace sgm;
+
+namespace {
+
+constexpr int kTimingRing = 1024;
+
+const char *const kStageNames[kNumStages] = {"census", "aggregate", "wta_lr", "median", "uvmap"};
+
+int validate(int W, int H, int D, const sgm_params *p) {
+    if (!p || W < 1 || H < 1 || D < 1) return SGM_ERR_INVALID_ARG;
+    if (p->census_w < 1 || p->census_h < 1 || !(p->census_w & 1) || !(p->census_h & 1))
+        return SGM_ERR_INVALID_ARG;
+    if (p->path_mask <= 0 || p->path_mask > 0xFF) return SGM_ERR_INVALID_ARG;
+    if (p->P1 < 0 || p->P2 < p->P1) return SGM_ERR_INVALID_ARG;
+    if (p->row_pitch != 0 && p->row_pitch < W) return SGM_ERR_INVALID_ARG;
+    if (p->median_k < 0 || (p->median_k > 1 && !(p->median_k & 1))) return SGM_ERR_INVALID_ARG;
+    const int nbits = p->census_w * p->census_h - 1;
+    if (nbits > 64) return SGM_ERR_UNSUPPORTED;
+    if (nbits + p->P2 > 255) return SGM_ERR_UNSUPPORTED;  // L_r must fit a byte
+    if (D > kMaxD || W > kMaxW || H > 65535) return SGM_ERR_UNSUPPORTED;
+    if (p->median_k > 7) return SGM_ERR_UNSUPPORTED;
+    return SGM_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+PathJobs make_jobs(const sgm_handle_s *h, int only_r) {
+    PathJobs j;
+    memset(&j, 0, sizeof(j));
+    // Longest scanlines first so that they start in the first wave.
+    int order[kMaxPaths], n = 0;
+    const bool wide = h->W >= h->H;
+    const int pref[kMaxPaths] = {wide ? 0 : 2, wide ? 1 : 3, wide ? 2 : 0, wide ? 3 : 1, 4, 5, 6, 7};
+    for (int i = 0; i < kMaxPaths; i++) {
+        const int r = pref[i];
+        if (only_r >= 0 ? r == only_r : (h->p.path_mask >> r) & 1) order[n++] = r;
+    }
+    j.n = n;
+    j.begin[0] = 0;
+    for (int k = 0; k < n; k++) {
+        const int r = order[k];
+        j.dx[k] = dir_dx(r);
+        j.dy[k] = dir_dy(r);
+        int plane = 0;
+        if (only_r < 0)
+            for (int q = 0; q < h->npaths; q++)
+                if (h->path_of_plane[q] == r) plane = q;
+        j.plane[k] = plane;
+        j.begin[k + 1] = j.begin[k] + (int)scanlines_of(r, h->W, h->H);
+    }
+    return j;
+}
+
+// ---- stage timing --------------------------------------------------------
+
+void harvest(sgm_handle_s *h, TimingRecord &rec) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(rec.stop) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, rec.start, rec.stop) == cudaSuccess) {
+        h->acc_ms[rec.stage] += ms;
+        h->acc_n[rec.stage] += 1;
+    }
+}
+
+TimingRecord *stage_begin(sgm_handle_s *h, int stage, cudaStream_t s) {
+    if (!h->timing || !h->recs) return nullptr;
+    TimingRecord *rec;
+    if (h->rec_count == kTimingRing) {  // ring full: fold the oldest record first
+        rec = &h->recs[h->rec_head];
+        harvest(h, *rec);
+        h->rec_head = (h->rec_head + 1) % kTimingRing;
+        h->rec_count--;
+    }
+    rec = &h->recs[(h->rec_head + h->rec_count) % kTimingRing];
+    rec->stage = stage;
+    cudaEventRecord(rec->start, s);
+    return rec;
+}
+
+void stage_end(sgm_handle_s *h, TimingRecord *rec, cudaStream_t s) {
+    if (!rec) return;
+    cudaEventRecord(rec->stop, s);
+    h->rec_count++;
+}
+
+// ---- the pipeline -----------------------------------------------------------
+
+int run_census(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaStream_t s) {
+    const int pitch = h->p.row_pitch ? h->p.row_pitch : h->W;
+    TimingRecord *t = stage_begin(h, kStageCensus, s);
+    cudaError_t e = launch_census(left, right, pitch, h->W, h->H, h->p.census_w, h->p.census_h,
+                                  h->code_bytes, h->codes, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+int run_aggregate(sgm_handle_s *h, int only_r, uint8_t *planes, cudaStream_t s) {
+    PathJobs jobs = make_jobs(h, only_r);
+    TimingRecord *t = stage_begin(h, kStageAggregate, s);
+    cudaError_t e = launch_aggregate(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->p.P1,
+                                     h->p.P2, jobs, planes, (size_t)h->W * h->H * h->D, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+int run_wta(sgm_handle_s *h, uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum,
+            cudaStream_t s) {
+    TimingRecord *t = stage_begin(h, kStageWta, s);
+    cudaError_t e = launch_wta(h->planes, h->npaths, (size_t)h->W * h->H * h->D, h->W, h->H, h->D,
+                               h->p.lr_tolerance, h->disp_lr, dbg_left, dbg_right, dbg_sum, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+int run_median(sgm_handle_s *h, uint8_t *disp, cudaStream_t s) {
+    TimingRecord *t = stage_begin(h, kStageMedian, s);
+    cudaError_t e;
+    if (h->p.median_k <= 1)
+        e = cudaMemcpyAsync(disp, h->disp_lr, (size_t)h->W * h->H, cudaMemcpyDeviceToDevice, s);
+    else
+        e = launch_median(h->disp_lr, disp, h->W, h->H, h->p.median_k, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+int compute_on(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+               cudaStream_t s) {
+    int rc = run_census(h, left, right, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, -1, h->planes, s);
+    if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, nullptr, s);
+    if (rc == SGM_OK) rc = run_median(h, disp, s);
+    return rc;
+}
+
+int uv_on(sgm_handle_s *h, const uint8_t *disp, uint16_t *umap, uint16_t *vmap, cudaStream_t s) {
+    TimingRecord *t = stage_begin(h, kStageUv, s);
+    cudaError_t e = launch_uvmap(disp, h->W, h->H, h->D, umap, vmap, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+void free_handle(sgm_handle_s *h) {
+    if (!h) return;
+    cudaFree(h->codes);
+    cudaFree(h->planes);
+    cudaFree(h->disp_lr);
+    cudaFree(h->io_left);
+    cudaFree(h->io_right);
+    cudaFree(h->io_disp);
+    cudaFree(h->io_umap);
+    cudaFree(h->io_vmap);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->recs) {
+        for (int i = 0; i < kTimingRing; i++) {
+            cudaEventDestroy(h->recs[i].start);
+            cudaEventDestroy(h->recs[i].stop);
+        }
+        free(h->recs);
+    }
+    free(h);
+}
+
+template <typename T>
+int dev_alloc(T **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) return SGM_OK;
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? SGM_ERR_OOM : SGM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sgm_status_string(int status) {
+    switch (status) {
+        case SGM_OK: return "ok";
+        case SGM_ERR_INVALID_ARG: return "invalid argument";
+        case SGM_ERR_UNSUPPORTED: return "unsupported parameters";
+        case SGM_ERR_OOM: return "out of memory";
+        case SGM_ERR_CUDA: return "CUDA error";
+        case SGM_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char *sgm_stage_name(int i) { return (i >= 0 && i < kNumStages) ? kStageNames[i] : nullptr; }
+
+int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
+    if (!out) return SGM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(W, H, D, params);
+    if (rc != SGM_OK) return rc;
+    sgm_handle_s *h = (sgm_handle_s *)calloc(1, sizeof(sgm_handle_s));
+    if (!h) return SGM_ERR_OOM;
+    h->W = W;
+    h->H = H;
+    h->D = D;
+    h->p = *params;
+    h->nbits = params->census_w * params->census_h - 1;
+    h->code_bytes = h->nbits <= 32 ? 4 : 8;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        free(h);
+        cudaGetLastError();
+        return SGM_ERR_CUDA;
+    }
+    for (int r = 0; r < kMaxPaths; r++)
+        if ((params->path_mask >> r) & 1) h->path_of_plane[h->npaths++] = r;
+    const size_t npx = (size_t)W * H;
+    rc = dev_alloc(&h->codes, 2 * npx * h->code_bytes);
+    if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * D);
+    if (rc == SGM_OK) rc = dev_alloc(&h->disp_lr, npx);
+    if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    if (rc == SGM_OK && (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess))
+        rc = SGM_ERR_CUDA;
+    if (rc != SGM_OK) {
+        cudaGetLastError();
+        free_handle(h);
+        return rc;
+    }
+    *out = h;
+    return SGM_OK;
+}
+
+int sgm_destroy(sgm_handle h) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    free_handle(h);
+    return SGM_OK;
+}
+
+int sgm_get_shape(sgm_handle h, int *W, int *H, int *D, int *census_bits) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    if (W) *W = h->W;
+    if (H) *H = h->H;
+    if (D) *D = h->D;
+    if (census_bits) *census_bits = h->nbits;
+    return SGM_OK;
+}
+
+int sgm_compute(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                void *stream) {
+    if (!h || !left || !right || !disp) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    return compute_on(h, left, right, disp, (cudaStream_t)stream);
+}
+
+int uvmap_compute(sgm_handle h, const uint8_t *disp, uint16_t *umap, uint16_t *vmap, void *stream) {
+    if (!h || !disp || !umap || !vmap) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    return uv_on(h, disp, umap, vmap, (cudaStream_t)stream);
+}
+
+int sgm_compute_host(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                     uint16_t *umap, uint16_t *vmap, void *stream) {
+    if (!h || !left || !right || !disp || (!umap) != (!vmap)) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    const size_t npx = (size_t)h->W * h->H;
+    int rc = SGM_OK;
+    if (!h->io_left) {
+        rc = dev_alloc(&h->io_left, npx);
+        if (rc == SGM_OK) rc = dev_alloc(&h->io_right, npx);
+        if (rc == SGM_OK) rc = dev_alloc(&h->io_disp, npx);
+        if (rc == SGM_OK) rc = dev_alloc(&h->io_umap, (size_t)h->D * h->W * sizeof(uint16_t));
+        if (rc == SGM_OK) rc = dev_alloc(&h->io_vmap, (size_t)h->H * h->D * sizeof(uint16_t));
+        if (rc != SGM_OK) {
+            cudaFree(h->io_left);
+            cudaFree(h->io_right);
+            cudaFree(h->io_disp);
+            cudaFree(h->io_umap);
+            cudaFree(h->io_vmap);
+            h->io_left = h->io_right = h->io_disp = nullptr;
+            h->io_umap = h->io_vmap = nullptr;
+            return rc;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // The handle's own input buffers are dense (pitch W).
+    const int saved_pitch = h->p.row_pitch;
+    h->p.row_pitch = 0;
+    if (cudaMemcpyAsync(h->io_left, left, npx, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->io_right, right, npx, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    if (rc == SGM_OK) rc = compute_on(h, h->io_left, h->io_right, h->io_disp, s);
+    h->p.row_pitch = saved_pitch;
+    if (rc == SGM_OK && umap) rc = uv_on(h, h->io_disp, h->io_umap, h->io_vmap, s);
+    if (rc == SGM_OK && cudaMemcpyAsync(disp, h->io_disp, npx, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    if (rc == SGM_OK && umap) {
+        if (cudaMemcpyAsync(umap, h->io_umap, (size_t)h->D * h->W * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(vmap, h->io_vmap, (size_t)h->H * h->D * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = SGM_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == SGM_OK) rc = SGM_ERR_CUDA;
+    return rc;
+}
+
+int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
+                      const uint8_t *const *right, uint8_t *const *disp, uint16_t *const *umap,
+                      uint16_t *const *vmap, void *stream) {
+    if (n < 0 || (n > 0 && (!hs || !left || !right || !disp))) return SGM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!hs[i] || !left[i] || !right[i] || !disp[i]) return SGM_ERR_INVALID_ARG;
+        if (umap && vmap && ((!umap[i]) != (!vmap[i]))) return SGM_ERR_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (hs[j] == hs[i]) return SGM_ERR_INVALID_ARG;
+    }
+    if (n == 0) return SGM_OK;
+    DeviceGuard g(hs[0]->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = SGM_OK;
+    for (int i = 0; i < n && rc == SGM_OK; i++) {
+        sgm_handle_s *h = hs[i];
+        if (h->device != hs[0]->device) return SGM_ERR_INVALID_ARG;
+        if (cudaEventRecord(h->fork_ev, s) != cudaSuccess ||
+            cudaStreamWaitEvent(h->side, h->fork_ev, 0) != cudaSuccess) {
+            rc = SGM_ERR_CUDA;
+            break;
+        }
+        rc = compute_on(h, left[i], right[i], disp[i], h->side);
+        if (rc == SGM_OK && umap && umap[i]) rc = uv_on(h, disp[i], umap[i], vmap[i], h->side);
+    }
+    // Join every side stream that was forked, whatever happened.
+    for (int i = 0; i < n; i++) {
+        sgm_handle_s *h = hs[i];
+        if (cudaEventRecord(h->join_ev, h->side) != cudaSuccess ||
+            cudaStreamWaitEvent(s, h->join_ev, 0) != cudaSuccess)
+            rc = rc == SGM_OK ? SGM_ERR_CUDA : rc;
+    }
+    return rc;
+}
+
+int sgm_debug_census(sgm_handle h, const uint8_t *left, const uint8_t *right, uint64_t *codes_left,
+                     uint64_t *codes_right, void *stream) {
+    if (!h || !left || !right || !codes_left || !codes_right) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = run_census(h, left, right, s);
+    if (rc != SGM_OK) return rc;
+    const size_t npx = (size_t)h->W * h->H;
+    if (h->code_bytes == 8) {
+        if (cudaMemcpyAsync(codes_left, h->codes, npx * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(codes_right, (uint8_t *)h->codes + npx * 8, npx * 8,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return SGM_ERR_CUDA;
+    } else {
+        // widen 32-bit codes: zero the outputs, then copy into the low halves
+        if (cudaMemsetAsync(codes_left, 0, npx * 8, s) != cudaSuccess ||
+            cudaMemsetAsync(codes_right, 0, npx * 8, s) != cudaSuccess ||
+            cudaMemcpy2DAsync(codes_left, 8, h->codes, 4, 4, npx, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpy2DAsync(codes_right, 8, (uint8_t *)h->codes + npx * 4, 4, 4, npx,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return SGM_ERR_CUDA;
+    }
+    return SGM_OK;
+}
+
+int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *right, uint8_t *L,
+                   void *stream) {
+    if (!h || !left || !right || !L || r < 0 || r >= kMaxPaths) return SGM_ERR_INVALID_ARG;
+    if (!((h->p.path_mask >> r) & 1)) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = run_census(h, left, right, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, r, L, s);
+    return rc;
+}
+
+int sgm_debug_sum(sgm_handle h, const uint8_t *left, const uint8_t *right, uint16_t *S, void *stream) {
+    if (!h || !left || !right || !S) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = run_census(h, left, right, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, -1, h->planes, s);
+    if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, S, s);
+    return rc;
+}
+
+int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp_left,
+                  uint8_t *disp_right, uint8_t *disp_lr, void *stream) {
+    if (!h || !left || !right) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = run_census(h, left, right, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, -1, h->planes, s);
+    if (rc == SGM_OK) rc = run_wta(h, disp_left, disp_right, nullptr, s);
+    if (rc == SGM_OK && disp_lr &&
+        cudaMemcpyAsync(disp_lr, h->disp_lr, (size_t)h->W * h->H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    return rc;
+}
+
+int sgm_set_timing(sgm_handle h, int enable) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (enable && !h->recs) {
+        TimingRecord *recs = (TimingRecord *)calloc(kTimingRing, sizeof(TimingRecord));
+        if (!recs) return SGM_ERR_OOM;
+        for (int i = 0; i < kTimingRing; i++) {
+            if (cudaEventCreate(&recs[i].start) != cudaSuccess ||
+                cudaEventCreate(&recs[i].stop) != cudaSuccess) {
+                for (int j = 0; j <= i; j++) {
+                    if (recs[j].start) cudaEventDestroy(recs[j].start);
+                    if (recs[j].stop) cudaEventDestroy(recs[j].stop);
+                }
+                free(recs);
+                cudaGetLastError();
+                return SGM_ERR_CUDA;
+            }
+        }
+        h->recs = recs;
+        h->rec_head = h->rec_count = 0;
+    }
+    h->timing = enable ? 1 : 0;
+    return SGM_OK;
+}
+
+int sgm_get_stage_times(sgm_handle h, float *ms, int *count, int n, int *n_stages) {
+    if (!h || n < 0) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    while (h->rec_count > 0) {
+        harvest(h, h->recs[h->rec_head]);
+        h->rec_head = (h->rec_head + 1) % kTimingRing;
+        h->rec_count--;
+    }
+    for (int i = 0; i < n && i < kNumStages; i++) {
+        if (ms) ms[i] = (float)h->acc_ms[i];
+        if (count) count[i] = h->acc_n[i];
+    }
+    for (int i = 0; i < kNumStages; i++) {
+        h->acc_ms[i] = 0;
+        h->acc_n[i] = 0;
+    }
+    if (n_stages) *n_stages = kNumStages;
+    return SGM_OK;
+}
+
+}  // extern "C"

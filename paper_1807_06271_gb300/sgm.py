@@ -1,0 +1,299 @@
+"""Python binding of libsgm (ctypes).  Argument marshalling only: every step
+of the method runs in the CUDA library; there is no CPU fallback.
+
+Device buffers are torch CUDA tensors (uint8 images and disparities, uint16
+maps, int64/uint64 census codes); the stream defaults to torch's current
+stream.  Function names follow the C ABI in ``include/sgm.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+SGM_OK = 0
+SGM_ERR_INVALID_ARG = 1
+SGM_ERR_UNSUPPORTED = 2
+SGM_ERR_OOM = 3
+SGM_ERR_CUDA = 4
+SGM_ERR_TIMEOUT = 5
+SGM_INVALID = 0xFF
+
+SGM_PATHS_4 = 0x0F
+SGM_PATHS_8 = 0xFF
+SGM_PATHS_STREAM4 = 0x55
+
+STAGES = ("census", "aggregate", "wta_lr", "median", "uvmap")
+
+
+class SgmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("census_w", ctypes.c_int), ("census_h", ctypes.c_int),
+                ("path_mask", ctypes.c_int), ("P1", ctypes.c_int), ("P2", ctypes.c_int),
+                ("lr_tolerance", ctypes.c_int), ("median_k", ctypes.c_int),
+                ("row_pitch", ctypes.c_int)]
+
+
+@dataclass
+class SgmParams:
+    census_w: int = 5
+    census_h: int = 5
+    path_mask: int = SGM_PATHS_8
+    P1: int = 8
+    P2: int = 32
+    lr_tolerance: int = 1
+    median_k: int = 5
+    row_pitch: int = 0
+
+    def _c(self) -> _Params:
+        return _Params(self.census_w, self.census_h, self.path_mask, self.P1, self.P2,
+                       self.lr_tolerance, self.median_k, self.row_pitch)
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+_SIGNATURES = {
+    "sgm_create": [_I, _I, _I, ctypes.POINTER(_Params), ctypes.POINTER(_P)],
+    "sgm_destroy": [_P],
+    "sgm_compute": [_P, _P, _P, _P, _P],
+    "uvmap_compute": [_P, _P, _P, _P, _P],
+    "sgm_compute_host": [_P, _P, _P, _P, _P, _P, _P],
+    "sgm_batch_compute": [_I, _P, _P, _P, _P, _P, _P, _P],
+    "sgm_get_shape": [_P, _P, _P, _P, _P],
+    "sgm_debug_census": [_P, _P, _P, _P, _P, _P],
+    "sgm_debug_path": [_P, _I, _P, _P, _P, _P],
+    "sgm_debug_sum": [_P, _P, _P, _P, _P],
+    "sgm_debug_raw": [_P, _P, _P, _P, _P, _P, _P],
+    "sgm_set_timing": [_P, _I],
+    "sgm_get_stage_times": [_P, _P, _P, _I, _P],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsgm.so (building it with nvcc when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsgm.so not found at {path}; build it with "
+                           "`python -m paper_1807_06271_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.sgm_status_string.argtypes = [_I]
+    lib.sgm_status_string.restype = ctypes.c_char_p
+    lib.sgm_stage_name.argtypes = [_I]
+    lib.sgm_stage_name.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().sgm_status_string(status).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != SGM_OK:
+        raise SgmError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t, dtype_names, shape, what):
+    """Pointer of a contiguous CUDA tensor with the expected dtype and size."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what}: expected a CUDA tensor")
+    if str(t.dtype).replace("torch.", "") not in dtype_names:
+        raise ValueError(f"{what}: dtype {t.dtype} not in {dtype_names}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t.data_ptr()
+
+
+class Handle:
+    """Owns one sgm_handle (W x H images, D disparities, fixed parameters)."""
+
+    def __init__(self, W: int, H: int, D: int, params: SgmParams | None = None):
+        self.W, self.H, self.D = W, H, D
+        self.params = params or SgmParams()
+        self._h = sgm_create(W, H, D, self.params)
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            sgm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _img_shape(self):
+        pitch = self.params.row_pitch or self.W
+        return (self.H, pitch)
+
+    def compute(self, left, right, disp, stream=None):
+        sgm_compute(self, left, right, disp, stream)
+
+    def uvmap(self, disp, umap, vmap, stream=None):
+        uvmap_compute(self, disp, umap, vmap, stream)
+
+
+def _hptr(h):
+    return h.ptr if isinstance(h, Handle) else h
+
+
+def sgm_create(W: int, H: int, D: int, params: SgmParams):
+    out = _P()
+    p = params._c()
+    _check(load().sgm_create(W, H, D, ctypes.byref(p), ctypes.byref(out)), "sgm_create")
+    return out.value
+
+
+def sgm_destroy(h):
+    _check(load().sgm_destroy(_hptr(h)), "sgm_destroy")
+
+
+def sgm_compute(h: Handle, left, right, disp, stream=None):
+    shp = h._img_shape()
+    _check(load().sgm_compute(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
+        _dev(disp, ("uint8",), (h.H, h.W), "disp"), _stream(stream)), "sgm_compute")
+
+
+def uvmap_compute(h: Handle, disp, umap, vmap, stream=None):
+    _check(load().uvmap_compute(
+        h.ptr, _dev(disp, ("uint8",), (h.H, h.W), "disp"),
+        _dev(umap, ("uint16", "int16"), (h.D, h.W), "umap"),
+        _dev(vmap, ("uint16", "int16"), (h.H, h.D), "vmap"), _stream(stream)), "uvmap_compute")
+
+
+def _host(t, nbytes, what):
+    """Pointer of a host buffer (numpy array or CPU tensor) of nbytes bytes."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if t.is_cuda or not t.is_contiguous() or t.numel() * t.element_size() != nbytes:
+            raise ValueError(f"{what}: expected a contiguous host tensor of {nbytes} bytes")
+        return t.data_ptr()
+    if not t.flags["C_CONTIGUOUS"] or t.nbytes != nbytes:
+        raise ValueError(f"{what}: expected a contiguous array of {nbytes} bytes")
+    return t.ctypes.data
+
+
+def sgm_compute_host(h: Handle, left, right, disp, umap=None, vmap=None, stream=None):
+    npx = h.W * h.H
+    _check(load().sgm_compute_host(
+        h.ptr, _host(left, npx, "left"), _host(right, npx, "right"), _host(disp, npx, "disp"),
+        _host(umap, 2 * h.D * h.W, "umap"), _host(vmap, 2 * h.H * h.D, "vmap"),
+        _stream(stream)), "sgm_compute_host")
+
+
+def sgm_batch_compute(handles, lefts, rights, disps, umaps=None, vmaps=None, stream=None):
+    n = len(handles)
+    arr = lambda T, xs: (T * n)(*xs)
+    hs = arr(_P, [h.ptr for h in handles])
+    L = arr(_P, [_dev(t, ("uint8",), h._img_shape(), "left") for h, t in zip(handles, lefts)])
+    R = arr(_P, [_dev(t, ("uint8",), h._img_shape(), "right") for h, t in zip(handles, rights)])
+    Dd = arr(_P, [_dev(t, ("uint8",), (h.H, h.W), "disp") for h, t in zip(handles, disps)])
+    U = V = None
+    if umaps is not None:
+        U = arr(_P, [_dev(t, ("uint16", "int16"), (h.D, h.W), "umap") if t is not None else None
+                     for h, t in zip(handles, umaps)])
+        V = arr(_P, [_dev(t, ("uint16", "int16"), (h.H, h.D), "vmap") if t is not None else None
+                     for h, t in zip(handles, vmaps)])
+    _check(load().sgm_batch_compute(n, hs, L, R, Dd, U, V, _stream(stream)), "sgm_batch_compute")
+
+
+def sgm_get_shape(h: Handle):
+    W, H, D, B = _I(), _I(), _I(), _I()
+    _check(load().sgm_get_shape(h.ptr, ctypes.byref(W), ctypes.byref(H), ctypes.byref(D),
+                                ctypes.byref(B)), "sgm_get_shape")
+    return W.value, H.value, D.value, B.value
+
+
+def sgm_debug_census(h: Handle, left, right, codes_left, codes_right, stream=None):
+    shp = h._img_shape()
+    _check(load().sgm_debug_census(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
+        _dev(codes_left, ("int64", "uint64"), (h.H, h.W), "codes_left"),
+        _dev(codes_right, ("int64", "uint64"), (h.H, h.W), "codes_right"), _stream(stream)),
+        "sgm_debug_census")
+
+
+def sgm_debug_path(h: Handle, r: int, left, right, L, stream=None):
+    shp = h._img_shape()
+    _check(load().sgm_debug_path(
+        h.ptr, r, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
+        _dev(L, ("uint8",), (h.H, h.W, h.D), "L"), _stream(stream)), "sgm_debug_path")
+
+
+def sgm_debug_sum(h: Handle, left, right, S, stream=None):
+    shp = h._img_shape()
+    _check(load().sgm_debug_sum(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
+        _dev(S, ("uint16", "int16"), (h.H, h.W, h.D), "S"), _stream(stream)), "sgm_debug_sum")
+
+
+def sgm_debug_raw(h: Handle, left, right, disp_left=None, disp_right=None, disp_lr=None,
+                  stream=None):
+    shp = h._img_shape()
+    px = (h.H, h.W)
+    _check(load().sgm_debug_raw(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
+        _dev(disp_left, ("uint8",), px, "disp_left"), _dev(disp_right, ("uint8",), px, "disp_right"),
+        _dev(disp_lr, ("uint8",), px, "disp_lr"), _stream(stream)), "sgm_debug_raw")
+
+
+def sgm_set_timing(h: Handle, enable: bool):
+    _check(load().sgm_set_timing(h.ptr, 1 if enable else 0), "sgm_set_timing")
+
+
+def sgm_get_stage_times(h: Handle):
+    """{stage: (total_ms, launches)} since the previous read."""
+    n = len(STAGES)
+    ms = (ctypes.c_float * n)()
+    cnt = (ctypes.c_int * n)()
+    ns = _I()
+    _check(load().sgm_get_stage_times(h.ptr, ms, cnt, n, ctypes.byref(ns)), "sgm_get_stage_times")
+    return {STAGES[i]: (ms[i], cnt[i]) for i in range(min(n, ns.value))}

@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads without a GPU, exports every symbol that
+include/sgm.h declares, and rejects bad arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1807_06271_gb300 import sgm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"^\s*(?:const\s+)?(?:int|char|void)\s*\*?\s*(\w+)\s*\(", text, re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("sgm_create", "sgm_compute", "uvmap_compute", "sgm_destroy",
+                 "sgm_batch_compute", "sgm_status_string", "sgm_debug_path"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sgm.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    assert sgm.status_string(sgm.SGM_OK) == "ok"
+    assert "invalid" in sgm.status_string(sgm.SGM_ERR_INVALID_ARG)
+    assert sgm.status_string(999) == "unknown status"
+
+
+def _create(W, H, D, **kw):
+    p = sgm.SgmParams(**kw)._c()
+    out = ctypes.c_void_p()
+    rc = sgm.load().sgm_create(W, H, D, ctypes.byref(p), ctypes.byref(out))
+    return rc, out.value
+
+
+@pytest.mark.parametrize("W,H,D,kw,want", [
+    (0, 10, 16, {}, sgm.SGM_ERR_INVALID_ARG),             # empty image
+    (10, 0, 16, {}, sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 0, {}, sgm.SGM_ERR_INVALID_ARG),              # no disparities
+    (10, 10, 256, {}, sgm.SGM_ERR_UNSUPPORTED),            # d would collide with 0xFF
+    (10, 10, 16, dict(census_w=4), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(census_w=9, census_h=9), sgm.SGM_ERR_UNSUPPORTED),  # 80 bits
+    (10, 10, 16, dict(P1=9, P2=8), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(P1=-1), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(census_w=9, census_h=7, P2=200), sgm.SGM_ERR_UNSUPPORTED),  # 62+200 > 255
+    (10, 10, 16, dict(path_mask=0), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(path_mask=0x100), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(median_k=4), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(median_k=9), sgm.SGM_ERR_UNSUPPORTED),
+    (10, 10, 16, dict(row_pitch=5), sgm.SGM_ERR_INVALID_ARG),
+    (9000, 10, 16, {}, sgm.SGM_ERR_UNSUPPORTED),
+])
+def test_create_rejects_bad_arguments_on_host(W, H, D, kw, want):
+    rc, h = _create(W, H, D, **kw)
+    assert rc == want and h is None
+
+
+def test_null_arguments_are_rejected():
+    lib = sgm.load()
+    assert lib.sgm_create(10, 10, 16, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_compute(None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.uvmap_compute(None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_destroy(None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_batch_compute(-1, None, None, None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_batch_compute(0, None, None, None, None, None, None, None) == sgm.SGM_OK
+    assert lib.sgm_stage_name(0) == b"census"
+    assert lib.sgm_stage_name(99) is None
+
+
+def test_binding_has_the_c_names():
+    for n in declared_functions():
+        if n in ("sgm_status_string", "sgm_stage_name"):
+            continue
+        assert hasattr(sgm, n), n

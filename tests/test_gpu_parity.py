@@ -1,0 +1,257 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+All arithmetic is integer, so every stage must match bit-exactly: census
+codes, each path's L_r, the sum S, the left/right winners, the LR-checked map,
+the median-filtered map and the U-/V-maps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_06271_gb300 import scenes, sgm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, skipped there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def u16(t):
+    return t.cpu().numpy().view(np.uint16)
+
+
+def params(cw, ch, mask, P1, P2, tol, k, pitch=0):
+    return sgm.SgmParams(census_w=cw, census_h=ch, path_mask=mask, P1=P1, P2=P2,
+                         lr_tolerance=tol, median_k=k, row_pitch=pitch)
+
+
+def gpu_all(left, right, D, p):
+    H, W = left.shape
+    out = {}
+    with sgm.Handle(W, H, D, p) as h:
+        L, R = cuda(left), cuda(right)
+        cl = torch.empty((H, W), dtype=torch.int64, device="cuda")
+        cr = torch.empty_like(cl)
+        sgm.sgm_debug_census(h, L, R, cl, cr)
+        out["codes_l"] = cl.cpu().numpy().view(np.uint64)
+        out["codes_r"] = cr.cpu().numpy().view(np.uint64)
+        out["paths"] = {}
+        for r in range(8):
+            if (p.path_mask >> r) & 1:
+                Lr = torch.empty((H, W, D), dtype=torch.uint8, device="cuda")
+                sgm.sgm_debug_path(h, r, L, R, Lr)
+                out["paths"][r] = Lr.cpu().numpy()
+        S = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
+        sgm.sgm_debug_sum(h, L, R, S)
+        out["S"] = u16(S)
+        dl, dr, lr = (torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in range(3))
+        sgm.sgm_debug_raw(h, L, R, dl, dr, lr)
+        out["DL"], out["DR"], out["lr"] = dl.cpu().numpy(), dr.cpu().numpy(), lr.cpu().numpy()
+        disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        h.compute(L, R, disp)
+        U = torch.empty((D, W), dtype=torch.int16, device="cuda")
+        V = torch.empty((H, D), dtype=torch.int16, device="cuda")
+        h.uvmap(disp, U, V)
+        torch.cuda.synchronize()
+        out["disp"], out["U"], out["V"] = disp.cpu().numpy(), u16(U), u16(V)
+    return out
+
+
+def oracle_all(left, right, D, p):
+    o = oracle.sgm(left, right, D, p.census_w, p.census_h, p.path_mask, p.P1, p.P2,
+                   p.lr_tolerance, p.median_k, stages=True)
+    C = oracle.cost_volume(o["codes_l"], o["codes_r"], D, p.census_w * p.census_h - 1)
+    o["paths"] = {r: oracle.aggregate_path(C, r, p.P1, p.P2)
+                  for r in range(8) if (p.path_mask >> r) & 1}
+    return o
+
+
+def assert_same(g, o, what):
+    assert g.shape == o.shape, (what, g.shape, o.shape)
+    if not np.array_equal(g, o):
+        bad = np.argwhere(g != o)
+        i = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {i}: gpu {g[i]} oracle {o[i]}")
+
+
+def compare_all(left, right, D, p):
+    g, o = gpu_all(left, right, D, p), oracle_all(left, right, D, p)
+    assert_same(g["codes_l"], o["codes_l"], "census left")
+    assert_same(g["codes_r"], o["codes_r"], "census right")
+    for r in o["paths"]:
+        assert_same(g["paths"][r], o["paths"][r].astype(np.uint8), f"path {r}")
+    for k in ("S", "DL", "DR", "lr", "disp", "U", "V"):
+        assert_same(g[k], o[k], k)
+
+
+CASES = [
+    # W, H, D, cw, ch, mask, P1, P2, tol, k
+    (37, 23, 16, 5, 5, 0x0F, 4, 24, 1, 5),
+    (64, 33, 64, 9, 7, 0xFF, 8, 96, 1, 3),
+    (100, 7, 13, 3, 3, 0x55, 2, 9, 0, 0),
+    (5, 100, 33, 7, 9, 0xFF, 10, 60, 2, 7),
+    (129, 40, 128, 9, 7, 0xFF, 8, 96, 1, 3),
+    (70, 45, 129, 5, 5, 0xAA, 3, 30, 1, 5),
+    (300, 20, 255, 5, 5, 0x0F, 1, 200, 1, 3),
+    (1, 1, 1, 1, 1, 0x01, 0, 0, -1, 0),
+    (8, 8, 64, 5, 5, 0xFF, 4, 24, 1, 3),
+    (200, 1, 32, 5, 5, 0x0F, 4, 24, 1, 3),
+    (1, 50, 8, 5, 5, 0x0F, 4, 24, 1, 3),
+    (33, 17, 60, 5, 5, 0x55, 8, 32, 1, 5),
+    (97, 61, 100, 9, 7, 0x3C, 7, 50, 1, 1),
+    (45, 31, 2, 3, 5, 0x81, 1, 1, 0, 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[:3])) + f"-m{c[5]:02x}")
+def test_stage_parity_textured(case):
+    W, H, D, cw, ch, mask, P1, P2, tol, k = case
+    s = scenes.boxes_scene(W, H, D, seed=W * 131 + H, n_boxes=3,
+                           dlo=min(2, D - 1), dhi=max(2, D - 1)) if min(W, H) >= 8 else None
+    if s is None:
+        r = np.random.default_rng(W + H + D)
+        left = r.integers(0, 256, (H, W)).astype(np.uint8)
+        right = r.integers(0, 256, (H, W)).astype(np.uint8)
+    else:
+        left, right = s.left, s.right
+    compare_all(left, right, D, params(cw, ch, mask, P1, P2, tol, k))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_stage_parity_random_masks_and_noise(seed):
+    r = np.random.default_rng(seed)
+    W, H = int(r.integers(20, 90)), int(r.integers(10, 60))
+    D = int(r.integers(1, 140))
+    cw, ch = [(3, 3), (5, 5), (9, 7), (7, 9), (5, 3)][seed % 5]
+    nb = cw * ch - 1
+    P2 = int(r.integers(0, 255 - nb))
+    P1 = int(r.integers(0, P2 + 1))
+    mask = int(r.integers(1, 256))
+    left = r.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.roll(left, 3, axis=1) ^ (r.random((H, W)) < 0.1).astype(np.uint8)
+    compare_all(left, right, D, params(cw, ch, mask, P1, P2, int(r.integers(-1, 3)),
+                                       [0, 1, 3, 5, 7][seed % 5]))
+
+
+def test_constant_images_degenerate_case():
+    left = np.full((30, 40), 90, np.uint8)
+    compare_all(left, left.copy(), 24, params(5, 5, 0xFF, 4, 24, 1, 3))
+
+
+def test_max_width_row():
+    W, H, D = 8192, 3, 64
+    r = np.random.default_rng(1)
+    left = r.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.roll(left, -5, axis=1)
+    p = params(5, 5, 0x0F, 4, 24, 1, 3)
+    o = oracle.sgm(left, right, D, 5, 5, 0x0F, 4, 24, 1, 3)
+    with sgm.Handle(W, H, D, p) as h:
+        disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        h.compute(cuda(left), cuda(right), disp)
+        assert_same(disp.cpu().numpy(), o["disp"], "disp")
+
+
+def test_row_pitch_and_side_stream():
+    W, H, D, pitch = 50, 20, 32, 64
+    s = scenes.boxes_scene(W, H, D, seed=3, n_boxes=2, dlo=2, dhi=30)
+    big_l = np.zeros((H, pitch), np.uint8)
+    big_r = np.full((H, pitch), 200, np.uint8)
+    big_l[:, :W], big_r[:, :W] = s.left, s.right
+    p = params(5, 5, 0xFF, 4, 24, 1, 3, pitch=pitch)
+    o = oracle.sgm(s.left, s.right, D, 5, 5, 0xFF, 4, 24, 1, 3)
+    st = torch.cuda.Stream()
+    with sgm.Handle(W, H, D, p) as h, torch.cuda.stream(st):
+        disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        h.compute(cuda(big_l), cuda(big_r), disp, stream=st)
+        st.synchronize()
+        assert_same(disp.cpu().numpy(), o["disp"], "disp with pitch")
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the configuration the benchmark times.
+# ---------------------------------------------------------------------------
+
+def _workload_params(w):
+    return params(w.census_w, w.census_h, w.path_mask, w.P1, w.P2, w.lr_tol, w.median_k)
+
+
+@pytest.mark.parametrize("name,idx", [("SMALL_320", 0), ("KITTI_1242", 1), ("HD_1280", 2),
+                                      ("PAPER_640", 5)])
+def test_full_size_workloads_bit_exact(name, idx):
+    w = getattr(scenes, name)
+    s = scenes.scene_for(w, scenes.workload_seed(idx))
+    p = _workload_params(w)
+    o = oracle.sgm(s.left, s.right, w.D, w.census_w, w.census_h, w.path_mask, w.P1, w.P2,
+                   w.lr_tol, w.median_k, stages=True)
+    with sgm.Handle(w.W, w.H, w.D, p) as h:
+        L, R = cuda(s.left), cuda(s.right)
+        disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
+        U = torch.empty((w.D, w.W), dtype=torch.int16, device="cuda")
+        V = torch.empty((w.H, w.D), dtype=torch.int16, device="cuda")
+        h.compute(L, R, disp)
+        h.uvmap(disp, U, V)
+        S = torch.empty((w.H, w.W, w.D), dtype=torch.int16, device="cuda")
+        sgm.sgm_debug_sum(h, L, R, S)
+        torch.cuda.synchronize()
+        assert_same(u16(S), o["S"], "S")
+        assert_same(disp.cpu().numpy(), o["disp"], "disp")
+        assert_same(u16(U), o["U"], "U")
+        assert_same(u16(V), o["V"], "V")
+
+
+def test_host_entry_point_matches_device_path():
+    w = scenes.SMALL_320
+    s = scenes.scene_for(w, scenes.workload_seed(0))
+    o = oracle.sgm(s.left, s.right, w.D, w.census_w, w.census_h, w.path_mask, w.P1, w.P2,
+                   w.lr_tol, w.median_k)
+    with sgm.Handle(w.W, w.H, w.D, _workload_params(w)) as h:
+        disp = np.empty((w.H, w.W), np.uint8)
+        U = np.empty((w.D, w.W), np.uint16)
+        V = np.empty((w.H, w.D), np.uint16)
+        for _ in range(2):
+            sgm.sgm_compute_host(h, s.left, s.right, disp, U, V)
+            assert_same(disp, o["disp"], "disp")
+            assert_same(U, o["U"], "U")
+            assert_same(V, o["V"], "V")
+
+
+def test_batch_of_mixed_sizes_matches_oracle():
+    specs = [(320, 240, 64), (160, 120, 32), (200, 90, 128), (64, 64, 16)]
+    hs, Ls, Rs, Ds, Us, Vs, want = [], [], [], [], [], [], []
+    p = params(9, 7, 0xFF, 8, 96, 1, 3)
+    for i, (W, H, D) in enumerate(specs):
+        s = scenes.ground_scene(W, H, D, seed=40 + i, n_obstacles=3, dlo=D // 6, dhi=(D * 6) // 7)
+        want.append(oracle.sgm(s.left, s.right, D, 9, 7, 0xFF, 8, 96, 1, 3))
+        hs.append(sgm.Handle(W, H, D, p))
+        Ls.append(cuda(s.left))
+        Rs.append(cuda(s.right))
+        Ds.append(torch.empty((H, W), dtype=torch.uint8, device="cuda"))
+        Us.append(torch.empty((D, W), dtype=torch.int16, device="cuda"))
+        Vs.append(torch.empty((H, D), dtype=torch.int16, device="cuda"))
+    sgm.sgm_batch_compute(hs, Ls, Rs, Ds, Us, Vs)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert_same(Ds[i].cpu().numpy(), want[i]["disp"], f"disp {i}")
+        assert_same(u16(Us[i]), want[i]["U"], f"U {i}")
+        assert_same(u16(Vs[i]), want[i]["V"], f"V {i}")
+    for h in hs:
+        h.close()
+
+
+def test_stage_timing_counts_launches():
+    w = scenes.SMALL_320
+    s = scenes.scene_for(w, scenes.workload_seed(0))
+    with sgm.Handle(w.W, w.H, w.D, _workload_params(w)) as h:
+        L, R = cuda(s.left), cuda(s.right)
+        disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
+        sgm.sgm_set_timing(h, True)
+        for _ in range(3):
+            h.compute(L, R, disp)
+        t = sgm.sgm_get_stage_times(h)
+        assert t["census"][1] == 3 and t["aggregate"][1] == 3 and t["wta_lr"][1] == 3
+        assert all(ms > 0 for ms, n in t.values() if n)
+        assert sgm.sgm_get_stage_times(h)["aggregate"][1] == 0

@@ -1,0 +1,48 @@
+"""Host logic of the multi-replica benchmark path on CPU: two gloo ranks,
+one pair each, max-over-ranks timing and whole-job throughput."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    r, w, _ = bench.dist_env()
+    seconds = 1.0 + r  # rank 1 is slower
+    smax = bench.reduce_max(seconds, w)
+    rate = bench.whole_job_rate(100.0, w, smax)
+    q.put((r, bench.rank_seed(1, r), smax, rate))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_max_time_and_distinct_pairs():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    out = sorted(q.get(timeout=10) for _ in range(2))
+    assert out[0][1] != out[1][1]          # each rank draws its own pair
+    assert out[0][2] == out[1][2] == 2.0   # max over ranks
+    assert out[0][3] == out[1][3] == 100.0  # 2 ranks x 100 units / 2 s

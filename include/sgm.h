@@ -148,6 +148,37 @@ int sgm_get_stage_times(sgm_handle h, float *ms, int *count, int n, int *n_stage
 /* Name of stage i ("census", "aggregate", ...), NULL when out of range. */
 const char *sgm_stage_name(int i);
 
+/* ---- no-allocation variant ------------------------------------------------ */
+
+/* Size in bytes of the device array that holds the scratch of
+ * sgm_compute_static.  Every GPU that loads the library reserves it when the
+ * library's device code is loaded there and keeps it until the process exits. */
+#define SGM_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* The disparity path of sgm_compute for one pair, with no handle and no
+ * device allocation.  The paper has no counterpart: this entry point is for
+ * callers that cannot call cudaMalloc, such as a camera loop with a hard
+ * per-frame deadline (an allocation may block or fail mid-flight), a host
+ * framework that owns all device memory through its own allocator, or code
+ * that must avoid the device synchronisation cudaFree implies.
+ *   Arguments and checks as sgm_create + sgm_compute: left/right are device
+ *   images of H rows of row_pitch bytes, disp is a device H x W byte map.
+ *   Scratch: census codes (2*W*H*4 bytes when census_w*census_h-1 <= 32, else
+ *   2*W*H*8), one W*H*D byte plane per enabled path and a W*H byte map, each
+ *   rounded up to 256 bytes.  A call that needs more than
+ *   SGM_STATIC_SCRATCH_BYTES returns SGM_ERR_UNSUPPORTED before any GPU work
+ *   (320x240 with D=64 and 4 paths needs about 20 MiB).
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ *   All calls on a device share the one array and leave their data in it
+ *   (nothing there needs to start at zero).  Calls whose work overlaps on the
+ *   GPU (other streams, other host threads) race and corrupt each other's
+ *   results: serialise them, e.g. on one stream.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+int sgm_compute_static(int W, int H, int D, const sgm_params *params,
+                       const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -198,6 +198,9 @@ int dev_alloc(T **p, size_t bytes) {
 
 }  // namespace
 
+// Same host-side argument checks as sgm_create, for entry points without a handle.
+int sgm::validate_params(int W, int H, int D, const sgm_params *p) { return validate(W, H, D, p); }
+
 extern "C" {
 
 const char *sgm_status_string(int status) {

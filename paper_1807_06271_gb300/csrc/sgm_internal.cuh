@@ -88,6 +88,9 @@ cudaError_t launch_wta(const uint8_t *planes, int nplanes, size_t plane_elems, i
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s);
 cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, cudaStream_t s);
+// Host-side argument checks shared by every entry point (SGM_OK or an error status).
+int validate_params(int W, int H, int D, const sgm_params *p);
+
 cudaError_t launch_uvmap(const uint8_t *disp, int W, int H, int D, uint16_t *umap, uint16_t *vmap,
                          cudaStream_t s);
 

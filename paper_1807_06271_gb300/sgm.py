@@ -75,7 +75,10 @@ _SIGNATURES = {
     "sgm_debug_raw": [_P, _P, _P, _P, _P, _P, _P],
     "sgm_set_timing": [_P, _I],
     "sgm_get_stage_times": [_P, _P, _P, _I, _P],
+    "sgm_compute_static": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P, _P],
 }
+
+SGM_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def library_path() -> str:
@@ -297,3 +300,16 @@ def sgm_get_stage_times(h: Handle):
     ns = _I()
     _check(load().sgm_get_stage_times(h.ptr, ms, cnt, n, ctypes.byref(ns)), "sgm_get_stage_times")
     return {STAGES[i]: (ms[i], cnt[i]) for i in range(min(n, ns.value))}
+
+
+def sgm_compute_static(W: int, H: int, D: int, params: SgmParams, left, right, disp, stream=None):
+    """sgm_compute without a handle or any device allocation (scratch in a fixed
+    device array of SGM_STATIC_SCRATCH_BYTES per GPU).  Calls that overlap on
+    the GPU race on that array; the first call on a device must not be made
+    inside a stream capture."""
+    shp = (H, params.row_pitch or W)
+    p = params._c()
+    _check(load().sgm_compute_static(
+        W, H, D, ctypes.byref(p), _dev(left, ("uint8",), shp, "left"),
+        _dev(right, ("uint8",), shp, "right"), _dev(disp, ("uint8",), (H, W), "disp"),
+        _stream(stream)), "sgm_compute_static")

@@ -164,10 +164,12 @@ const char *sgm_stage_name(int i);
  *   Arguments and checks as sgm_create + sgm_compute: left/right are device
  *   images of H rows of row_pitch bytes, disp is a device H x W byte map.
  *   Scratch: census codes (2*W*H*4 bytes when census_w*census_h-1 <= 32, else
- *   2*W*H*8), one W*H*D byte plane per enabled path and a W*H byte map, each
- *   rounded up to 256 bytes.  A call that needs more than
- *   SGM_STATIC_SCRATCH_BYTES returns SGM_ERR_UNSUPPORTED before any GPU work
- *   (320x240 with D=64 and 4 paths needs about 20 MiB).
+ *   2*W*H*8), a cost volume and one plane per enabled path of W*H*Dp bytes
+ *   each (Dp = D rounded up to 8 times a power of two: 8, 16, 32, 64, 128 or
+ *   256), a 256-byte work counter and a W*H byte map, each rounded up to 256
+ *   bytes.  A call that needs more than SGM_STATIC_SCRATCH_BYTES returns
+ *   SGM_ERR_UNSUPPORTED before any GPU work (320x240 with D=64 and 4 paths
+ *   needs about 25 MiB).
  *   The first call on a device looks up the array's device address with that
  *   device current; make that first call before any stream capture.
  *   All calls on a device share the one array and leave their data in it

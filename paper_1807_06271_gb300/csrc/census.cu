@@ -80,6 +80,76 @@ __global__ void __launch_bounds__(kBX *kBY)
     codes[(size_t)blockIdx.z * W * H + (size_t)y * W + x] = code;
 }
 
+// ---------------------------------------------------------------------------
+// Matching cost volume (Eq. 1): C(x,y,d) = popc(code_l(x,y) ^ code_r(x-d,y)),
+// or the code width when x-d < 0, for d < D; padding slots d >= D hold the
+// code width too.  One CTA per segment of kSeg pixels of one row: the
+// segment's left codes and the right codes it reaches (kSeg + Dp - 1 of them)
+// are staged in shared memory.  A thread computes one 8-disparity chunk of one
+// pixel, with consecutive threads on consecutive pixels so that the
+// shared-memory code reads are conflict-free; the segment is transposed
+// through a padded shared tile and written out with coalesced 8-byte stores
+// (the segment's Dp-byte pixel records are contiguous in global memory).
+// popc runs on the XU pipe (16 per SM per clock; two per estimate for 64-bit
+// codes), which bounds this kernel.
+// ---------------------------------------------------------------------------
+
+constexpr int kCostThreads = 256, kSeg = 64;
+
+__device__ __forceinline__ uint32_t popcnt(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ uint32_t popcnt(uint64_t v) { return __popcll(v); }
+
+template <typename CodeT, bool RAGGED>
+__global__ void __launch_bounds__(kCostThreads)
+    cost_kernel(const CodeT *__restrict__ codes, int W, int H, int D, int Dp, int nbits,
+                uint8_t *__restrict__ cost) {
+    extern __shared__ __align__(16) unsigned char cost_smem[];
+    const int stride = Dp + 8;  // padded tile row (bytes): conflict-free 8-byte tile writes
+    uint8_t *tile = cost_smem;                                         // [kSeg][stride]
+    CodeT *cl = reinterpret_cast<CodeT *>(cost_smem + kSeg * stride);  // [kSeg]
+    CodeT *cr = cl + kSeg;                                             // [kSeg + Dp - 1]
+    const int y = blockIdx.y, x0 = blockIdx.x * kSeg;
+    const int xr0 = x0 - (Dp - 1);  // right code cr[i] is column xr0 + i
+    const CodeT *rowl = codes + (size_t)y * W;
+    const CodeT *rowr = codes + (size_t)W * H + (size_t)y * W;
+    for (int i = threadIdx.x; i < kSeg; i += kCostThreads) cl[i] = x0 + i < W ? rowl[x0 + i] : 0;
+    for (int i = threadIdx.x; i < kSeg + Dp - 1; i += kCostThreads) {
+        const int xr = xr0 + i;
+        cr[i] = (xr >= 0 && xr < W) ? rowr[xr] : 0;
+    }
+    __syncthreads();
+    const int chunks = Dp / 8;
+    const bool border = x0 < Dp;  // only the first segments see x - d < 0
+    for (int it = threadIdx.x; it < kSeg * chunks; it += kCostThreads) {
+        const int px = it % kSeg, i = it / kSeg;
+        const int x = x0 + px;
+        const CodeT a = cl[px];
+        const CodeT *r = cr + px + Dp - 1 - 8 * i;  // right column x - d sits at r[-(d - 8i)]
+        uint32_t c[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) c[j] = popcnt(a ^ r[-j]);
+        if (RAGGED || border) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int d = 8 * i + j;
+                if ((RAGGED && d >= D) || x - d < 0) c[j] = (uint32_t)nbits;
+            }
+        }
+        uint2 v;
+        v.x = c[0] | (c[1] << 8) | (c[4] << 16) | (c[5] << 24);
+        v.y = c[2] | (c[3] << 8) | (c[6] << 16) | (c[7] << 24);
+        *reinterpret_cast<uint2 *>(tile + px * stride + 8 * i) = v;
+    }
+    __syncthreads();
+    const int npx = min(kSeg, W - x0);
+    uint8_t *out = cost + ((size_t)y * W + x0) * Dp;
+    for (int k = threadIdx.x; k < npx * chunks; k += kCostThreads) {
+        const int px = k / chunks, q = k - px * chunks;
+        *reinterpret_cast<uint2 *>(out + (size_t)px * Dp + 8 * q) =
+            *reinterpret_cast<const uint2 *>(tile + px * stride + 8 * q);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
@@ -96,6 +166,34 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
         else
             census_kernel_any<uint64_t><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint64_t *)codes);
     }
+    return cudaGetLastError();
+}
+
+}  // namespace sgm
+
+namespace sgm {
+
+cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
+                        uint8_t *cost, cudaStream_t s) {
+    const int Dp = padded_disparities(D);
+    const size_t smem = (size_t)kSeg * (Dp + 8) + (size_t)(2 * kSeg + Dp - 1) * code_bytes;
+    const dim3 grid((W + kSeg - 1) / kSeg, H);
+    cudaError_t e;
+    const bool rag = D != Dp;
+#define SGM_COST(T, R)                                                                                        \
+    do {                                                                                                      \
+        e = cudaFuncSetAttribute(cost_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                       \
+        cost_kernel<T, R><<<grid, kCostThreads, smem, s>>>((const T *)codes, W, H, D, Dp, nbits, cost);        \
+    } while (0)
+    if (code_bytes == 4) {
+        if (rag) SGM_COST(uint32_t, true);
+        else SGM_COST(uint32_t, false);
+    } else {
+        if (rag) SGM_COST(uint64_t, true);
+        else SGM_COST(uint64_t, false);
+    }
+#undef SGM_COST
     return cudaGetLastError();
 }
 

@@ -5,8 +5,8 @@
 // per-frame deadline, where an allocation can block or fail in mid-flight; a
 // host framework that owns all device memory through its own allocator and
 // forbids direct cudaMalloc/cudaFree; code that must not add the implicit
-// device synchronisation cudaFree brings.  For them the census codes, path
-// planes and LR map live in one file-scope device array of fixed size,
+// device synchronisation cudaFree brings.  For them the census codes, cost
+// volume, path planes and LR map live in one file-scope device array of fixed size,
 // reserved when the library's module is loaded on a device and held until
 // the process exits.  The kernels are the same ones sgm_compute runs.
 #include <mutex>
@@ -55,16 +55,17 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     if (rc != SGM_OK) return rc;
     const int nbits = params->census_w * params->census_h - 1;
     const int code_bytes = nbits <= 32 ? 4 : 8;
-    int npaths = 0;
-    int path_of_plane[sgm::kMaxPaths];
-    for (int r = 0; r < sgm::kMaxPaths; r++)
-        if ((params->path_mask >> r) & 1) path_of_plane[npaths++] = r;
+    const int npaths = __builtin_popcount((unsigned)params->path_mask);
+    const int Dp = sgm::padded_disparities(D);
 
-    // Scratch layout: codes | planes | LR map, each 256-byte aligned.
+    // Scratch layout: codes | cost volume | path planes | job counter | LR map,
+    // each 256-byte aligned.
     const size_t npx = (size_t)W * H;
     const size_t codes_off = 0;
-    const size_t planes_off = round_up(codes_off + 2 * npx * code_bytes, 256);
-    const size_t lr_off = round_up(planes_off + (size_t)npaths * npx * D, 256);
+    const size_t cost_off = round_up(codes_off + 2 * npx * code_bytes, 256);
+    const size_t planes_off = round_up(cost_off + npx * Dp, 256);
+    const size_t counter_off = round_up(planes_off + (size_t)npaths * npx * Dp, 256);
+    const size_t lr_off = counter_off + 256;
     const size_t need = lr_off + npx;
     if (need > (size_t)SGM_STATIC_SCRATCH_BYTES) return SGM_ERR_UNSUPPORTED;
 
@@ -72,36 +73,26 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     rc = scratch_for_current_device(&base);
     if (rc != SGM_OK) return rc;
     void *codes = base + codes_off;
+    uint8_t *cost = base + cost_off;
     uint8_t *planes = base + planes_off;
+    unsigned *counter = reinterpret_cast<unsigned *>(base + counter_off);
     uint8_t *disp_lr = base + lr_off;
+    const sgm::PathJobs jobs = sgm::make_path_jobs(W, H, D, params->path_mask);
 
-    // Scanline jobs over the enabled directions, longest scanlines first.
-    sgm::PathJobs jobs = {};
-    const bool wide = W >= H;
-    const int pref[sgm::kMaxPaths] = {wide ? 0 : 2, wide ? 1 : 3, wide ? 2 : 0, wide ? 3 : 1, 4, 5, 6, 7};
-    for (int i = 0; i < sgm::kMaxPaths; i++) {
-        const int r = pref[i];
-        if (!((params->path_mask >> r) & 1)) continue;
-        const int k = jobs.n++;
-        jobs.dx[k] = sgm::dir_dx(r);
-        jobs.dy[k] = sgm::dir_dy(r);
-        for (int q = 0; q < npaths; q++)
-            if (path_of_plane[q] == r) jobs.plane[k] = q;
-        jobs.begin[k + 1] = jobs.begin[k] + (int)sgm::scanlines_of(r, W, H);
-    }
-
-    // Every kernel below overwrites the scratch it later reads, so nothing
-    // left by an earlier call needs clearing.
+    // Every kernel below overwrites the scratch it later reads, and the job
+    // counter is cleared on the stream before the aggregation kernel, so
+    // nothing left by an earlier call needs clearing.
     cudaStream_t s = (cudaStream_t)stream;
     const int pitch = params->row_pitch ? params->row_pitch : W;
     cudaError_t e = sgm::launch_census(left, right, pitch, W, H, params->census_w, params->census_h,
                                        code_bytes, codes, s);
+    if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, s);
     if (e == cudaSuccess)
-        e = sgm::launch_aggregate(codes, code_bytes, W, H, D, nbits, params->P1, params->P2, jobs,
-                                  planes, npx * D, s);
+        e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, jobs, planes, npaths,
+                                  counter, 2, s);
     if (e == cudaSuccess)
-        e = sgm::launch_wta(planes, npaths, npx * D, W, H, D, params->lr_tolerance, disp_lr, nullptr,
-                            nullptr, nullptr, s);
+        e = sgm::launch_wta(planes, npaths, W, H, D, params->lr_tolerance, disp_lr, nullptr, nullptr,
+                            nullptr, s);
     if (e == cudaSuccess) {
         if (params->median_k <= 1)
             e = cudaMemcpyAsync(disp, disp_lr, npx, cudaMemcpyDeviceToDevice, s);

@@ -13,7 +13,7 @@ namespace {
 
 constexpr int kTimingRing = 1024;
 
-const char *const kStageNames[kNumStages] = {"census", "aggregate", "wta_lr", "median", "uvmap"};
+const char *const kStageNames[kNumStages] = {"census", "cost", "aggregate", "wta_lr", "median", "uvmap"};
 
 int validate(int W, int H, int D, const sgm_params *p) {
     if (!p || W < 1 || H < 1 || D < 1) return SGM_ERR_INVALID_ARG;
@@ -28,6 +28,10 @@ int validate(int W, int H, int D, const sgm_params *p) {
     if (nbits + p->P2 > 255) return SGM_ERR_UNSUPPORTED;  // L_r must fit a byte
     if (D > kMaxD || W > kMaxW || H > 65535) return SGM_ERR_UNSUPPORTED;
     if (p->median_k > 7) return SGM_ERR_UNSUPPORTED;
+    // kernels index the per-path planes with 32-bit counts of 8-byte chunks
+    const long long chunks = (long long)W * H * __builtin_popcount((unsigned)p->path_mask) *
+                             (padded_disparities(D) / 8);
+    if (chunks >= (1ll << 31)) return SGM_ERR_UNSUPPORTED;
     return SGM_OK;
 }
 
@@ -46,33 +50,6 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
-
-PathJobs make_jobs(const sgm_handle_s *h, int only_r) {
-    PathJobs j;
-    memset(&j, 0, sizeof(j));
-    // Longest scanlines first so that they start in the first wave.
-    int order[kMaxPaths], n = 0;
-    const bool wide = h->W >= h->H;
-    const int pref[kMaxPaths] = {wide ? 0 : 2, wide ? 1 : 3, wide ? 2 : 0, wide ? 3 : 1, 4, 5, 6, 7};
-    for (int i = 0; i < kMaxPaths; i++) {
-        const int r = pref[i];
-        if (only_r >= 0 ? r == only_r : (h->p.path_mask >> r) & 1) order[n++] = r;
-    }
-    j.n = n;
-    j.begin[0] = 0;
-    for (int k = 0; k < n; k++) {
-        const int r = order[k];
-        j.dx[k] = dir_dx(r);
-        j.dy[k] = dir_dy(r);
-        int plane = 0;
-        if (only_r < 0)
-            for (int q = 0; q < h->npaths; q++)
-                if (h->path_of_plane[q] == r) plane = q;
-        j.plane[k] = plane;
-        j.begin[k + 1] = j.begin[k] + (int)scanlines_of(r, h->W, h->H);
-    }
-    return j;
-}
 
 // ---- stage timing --------------------------------------------------------
 
@@ -117,11 +94,19 @@ int run_census(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaS
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
 
-int run_aggregate(sgm_handle_s *h, int only_r, uint8_t *planes, cudaStream_t s) {
-    PathJobs jobs = make_jobs(h, only_r);
+int run_cost(sgm_handle_s *h, cudaStream_t s) {
+    TimingRecord *t = stage_begin(h, kStageCost, s);
+    cudaError_t e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+// All enabled directions into h->planes, or direction only_r alone into plane 0.
+int run_aggregate(sgm_handle_s *h, int only_r, cudaStream_t s) {
+    const PathJobs jobs = make_path_jobs(h->W, h->H, h->D, only_r >= 0 ? (1 << only_r) : h->p.path_mask);
     TimingRecord *t = stage_begin(h, kStageAggregate, s);
-    cudaError_t e = launch_aggregate(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->p.P1,
-                                     h->p.P2, jobs, planes, (size_t)h->W * h->H * h->D, s);
+    cudaError_t e = launch_aggregate(h->cost, h->W, h->H, h->D, h->p.P1, h->p.P2, jobs, h->planes,
+                                     only_r >= 0 ? 1 : h->npaths, h->job_counter, h->agg_blocks_per_sm, s);
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
@@ -129,7 +114,7 @@ int run_aggregate(sgm_handle_s *h, int only_r, uint8_t *planes, cudaStream_t s) 
 int run_wta(sgm_handle_s *h, uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum,
             cudaStream_t s) {
     TimingRecord *t = stage_begin(h, kStageWta, s);
-    cudaError_t e = launch_wta(h->planes, h->npaths, (size_t)h->W * h->H * h->D, h->W, h->H, h->D,
+    cudaError_t e = launch_wta(h->planes, h->npaths, h->W, h->H, h->D,
                                h->p.lr_tolerance, h->disp_lr, dbg_left, dbg_right, dbg_sum, s);
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
@@ -149,7 +134,8 @@ int run_median(sgm_handle_s *h, uint8_t *disp, cudaStream_t s) {
 int compute_on(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
                cudaStream_t s) {
     int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_aggregate(h, -1, h->planes, s);
+    if (rc == SGM_OK) rc = run_cost(h, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
     if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, nullptr, s);
     if (rc == SGM_OK) rc = run_median(h, disp, s);
     return rc;
@@ -165,6 +151,8 @@ int uv_on(sgm_handle_s *h, const uint8_t *disp, uint16_t *umap, uint16_t *vmap, 
 void free_handle(sgm_handle_s *h) {
     if (!h) return;
     cudaFree(h->codes);
+    cudaFree(h->cost);
+    cudaFree(h->job_counter);
     cudaFree(h->planes);
     cudaFree(h->disp_lr);
     cudaFree(h->io_left);
@@ -237,9 +225,17 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     }
     for (int r = 0; r < kMaxPaths; r++)
         if ((params->path_mask >> r) & 1) h->path_of_plane[h->npaths++] = r;
+    h->Dp = padded_disparities(D);
+    h->agg_blocks_per_sm = 2;  // 8 resident warps per SM
+    if (const char *env = getenv("SGM_AGG_BLOCKS_PER_SM")) {  // tuning override
+        const int v = atoi(env);
+        if (v >= 1 && v <= 16) h->agg_blocks_per_sm = v;
+    }
     const size_t npx = (size_t)W * H;
     rc = dev_alloc(&h->codes, 2 * npx * h->code_bytes);
-    if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * D);
+    if (rc == SGM_OK) rc = dev_alloc(&h->cost, npx * h->Dp);
+    if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, sizeof(unsigned));
+    if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * h->Dp);
     if (rc == SGM_OK) rc = dev_alloc(&h->disp_lr, npx);
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
         rc = SGM_ERR_CUDA;
@@ -402,7 +398,10 @@ int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *righ
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_aggregate(h, r, L, s);
+    if (rc == SGM_OK) rc = run_cost(h, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, r, s);
+    if (rc == SGM_OK && launch_unpermute(h->planes, h->W, h->H, h->D, L, s) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
     return rc;
 }
 
@@ -412,7 +411,8 @@ int sgm_debug_sum(sgm_handle h, const uint8_t *left, const uint8_t *right, uint1
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_aggregate(h, -1, h->planes, s);
+    if (rc == SGM_OK) rc = run_cost(h, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
     if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, S, s);
     return rc;
 }
@@ -424,7 +424,8 @@ int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_aggregate(h, -1, h->planes, s);
+    if (rc == SGM_OK) rc = run_cost(h, s);
+    if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
     if (rc == SGM_OK) rc = run_wta(h, disp_left, disp_right, nullptr, s);
     if (rc == SGM_OK && disp_lr &&
         cudaMemcpyAsync(disp_lr, h->disp_lr, (size_t)h->W * h->H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

@@ -28,16 +28,39 @@ inline long scanlines_of(int r, int W, int H) {
     return (long)W + H - 1;
 }
 
-// Flattened list of scanlines over the enabled paths: warp g of the
-// aggregation launch works on scanline g - begin[k] of path entry k.
+// Disparity layout.  The D disparities of a pixel are handled by LPS lanes
+// ("lanes per scanline", a power of two) with 8 disparities each, so a pixel
+// owns Dp = 8 * LPS bytes in the cost volume and in every path plane; slots
+// d >= D are padding.  Inside each 8-byte lane chunk (disparities 8i .. 8i+7)
+// the bytes are stored in the order  d+0 d+1 d+4 d+5 | d+2 d+3 d+6 d+7  so
+// that masking a 32-bit word with 0x00FF00FF (directly or after >> 8) yields
+// the packed 16-bit pairs (d+k, d+k+4) the aggregation kernel works on.
+inline int lanes_per_scanline(int D) {
+    int need = (D + 7) / 8, l = 1;
+    while (l < need) l *= 2;
+    return l;
+}
+inline int padded_disparities(int D) { return 8 * lanes_per_scanline(D); }
+__host__ __device__ constexpr int chunk_byte_of(int j) {  // byte position of disparity 8i+j
+    return j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 4 : j == 3 ? 5 : j == 4 ? 2 : j == 5 ? 3 : j == 6 ? 6 : 7;
+}
+
+// Work list of the aggregation kernel: entry k is one enabled direction whose
+// nlines scanlines are cut into jobs of G = 32 / LPS neighbouring scanlines
+// (one warp each).  Job j belongs to entry k when jbegin[k] <= j < jbegin[k+1].
 struct PathJobs {
-    int n;                    // number of path entries
+    int n;                     // number of entries
     int dx[kMaxPaths], dy[kMaxPaths];
-    int plane[kMaxPaths];     // output plane of entry k
-    int begin[kMaxPaths + 1]; // prefix sums of scanline counts
+    int plane[kMaxPaths];      // output plane of entry k
+    int nlines[kMaxPaths];
+    int jbegin[kMaxPaths + 1];
 };
 
-enum Stage { kStageCensus = 0, kStageAggregate, kStageWta, kStageMedian, kStageUv, kNumStages };
+// Builds the work list for the directions in `mask` (planes numbered in
+// increasing direction order), longest scanlines first.
+PathJobs make_path_jobs(int W, int H, int D, int mask);
+
+enum Stage { kStageCensus = 0, kStageCost, kStageAggregate, kStageWta, kStageMedian, kStageUv, kNumStages };
 
 struct TimingRecord {
     int stage;
@@ -55,10 +78,15 @@ struct sgm_handle_s {
     int npaths;
     int path_of_plane[sgm::kMaxPaths];
 
+    int Dp;          // padded disparities per pixel (8 * lanes per scanline)
+
     // scratch, owned
     void *codes;        // [2][H][W] census codes (left, right)
-    uint8_t *planes;    // [npaths][H][W][D] per-path aggregated costs
+    uint8_t *cost;      // [H][W][Dp] matching cost, lane-chunk byte order
+    uint8_t *planes;    // [H][W][npaths][Dp] per-path aggregated costs, same byte order
     uint8_t *disp_lr;   // [H][W] after the LR check, before the median
+    unsigned *job_counter;  // work-queue head of the aggregation kernel
+    int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
 
     // device staging for sgm_compute_host, allocated on first use
     uint8_t *io_left, *io_right, *io_disp;
@@ -81,10 +109,16 @@ namespace sgm {
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
                           int cw, int ch, int code_bytes, void *codes, cudaStream_t s);
-cudaError_t launch_aggregate(const void *codes, int code_bytes, int W, int H, int D, int nbits,
-                             int P1, int P2, const PathJobs &jobs, uint8_t *planes,
-                             size_t plane_elems, cudaStream_t s);
-cudaError_t launch_wta(const uint8_t *planes, int nplanes, size_t plane_elems, int W, int H, int D,
+cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
+                        uint8_t *cost, cudaStream_t s);
+// Planes are pixel-interleaved: [H][W][nplanes][Dp], entry k of `jobs` writing
+// plane jobs.plane[k].  job_counter is cleared on s before the kernel starts.
+cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2,
+                             const PathJobs &jobs, uint8_t *planes, int nplanes,
+                             unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
+// Copies a single plane ([H][W][Dp], lane-chunk order) to L ([H][W][D], natural order).
+cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, uint8_t *L, cudaStream_t s);
+cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s);
 cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, cudaStream_t s);

@@ -1,67 +1,148 @@
 // Winner-takes-all on S = sum of the path planes (Sec. 3.1.3), the right
 // disparity taken from the same S (Sec. 3.1.4) and the left-right check.
 //
-// One CTA per image row.  A warp handles one pixel at a time with the
-// disparities across its lanes: it sums the path planes into S(x, d), forms
-// the key (S << 8) | d, reduces the left winner with one redux (ties go to
-// the smallest d because d sits in the low bits) and folds every key into
-// the right-disparity slot x - d with a shared-memory atomicMin, which gives
+// One CTA per image row.  The planes share the aggregation kernel's layout
+// (all planes of a pixel back to back): LPS lanes hold a pixel's
+// disparities, 8 per lane, so a warp covers G = 32 / LPS neighbouring
+// pixels.  A lane loads its 8-byte chunk of every plane at fixed offsets
+// from one pointer (all loads issued before any use), unpacks each into four packed
+// 16-bit pairs (d+k, d+k+4) with two masks and adds them: S <= 8 * 255 fits
+// 16 bits and no half carries.  For each disparity it forms the key
+// (S << 8) | d; the left winner is the minimum key over the pixel's lanes
+// (ties go to the smallest d, which sits in the low bits), and every key is
+// folded into slot x - d of a shared-memory array with atomicMin, which leaves
 // D_right(x') = argmin_d S(x' + d, d) with the same tie rule.  After a CTA
-// barrier the row's LR check runs from shared memory.
+// barrier the row's LR check runs from shared memory.  HBM traffic: the
+// planes once (npaths * Dp bytes per pixel) plus 1 byte written per pixel.
 #include "sgm_internal.cuh"
 
 namespace sgm {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr uint32_t kLo = 0x00FF00FFu;
 
-template <int DPL>
+// Minimum of v over the LPS lanes of this lane's pixel: one full-warp
+// redux.sync per pixel group, fed 0xFFFFFFFF by the other groups' lanes.
+template <int LPS>
+__device__ __forceinline__ uint32_t group_min(uint32_t v, int lane) {
+    constexpr int G = 32 / LPS;
+    if constexpr (LPS == 1) {
+        return v;
+    } else if constexpr (G == 1) {
+        return __reduce_min_sync(0xffffffffu, v);
+    } else {
+        const int grp = lane / LPS;
+        uint32_t m = 0;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            const uint32_t r = __reduce_min_sync(0xffffffffu, grp == g ? v : 0xFFFFFFFFu);
+            if (grp == g) m = r;
+        }
+        return m;
+    }
+}
+
+// The planes are read exactly once: keep them out of L1 and evict them first from L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint2 ld_plane(const uint8_t *p, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+// Sums the path planes of one pixel into four packed pairs S[k] = (S(d0+k), S(d0+k+4)),
+// folds its keys into the right-disparity slots and returns its smallest key.
+// The lane visits its 8 disparities in the order j ^ m with m = 2 * ((li >> 2) & 3),
+// which spreads the shared-memory atomics of a warp over distinct banks.
+template <int LPS, bool RAGGED, bool DEBUG>
+__device__ __forceinline__ uint32_t pixel_keys(const uint2 (&v)[kMaxPaths], int nplanes, bool active,
+                                               int x, int y, int W, int D, int li,
+                                               uint32_t *key_right, uint16_t *dbg_sum) {
+    uint32_t S[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < kMaxPaths; q++)
+        if (q < nplanes) {
+            S[0] += v[q].x & kLo;
+            S[1] += (v[q].x >> 8) & kLo;
+            S[2] += v[q].y & kLo;
+            S[3] += (v[q].y >> 8) & kLo;
+        }
+    const int d0 = 8 * li;
+    const bool sw_reg = (li >> 2) & 1, sw_half = (li >> 3) & 1;
+    const int m = (sw_reg ? 2 : 0) | (sw_half ? 4 : 0);
+    uint32_t T[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t a = sw_reg ? S[k ^ 2] : S[k];
+        T[k] = sw_half ? __byte_perm(a, a, 0x1032) : a;
+    }
+    uint32_t best = 0xFFFFFFFFu;
+    // every slot x - d of this lane lies in the row when x >= d0 + 7
+    const bool inside = active && x >= d0 + 7;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int d = d0 + (j ^ m);
+        const uint32_t sv = (j < 4) ? (T[j & 3] & 0xFFFFu) : (T[j & 3] >> 16);
+        uint32_t key = sv * 256u + (uint32_t)d;
+        if (RAGGED && d >= D) key = 0xFFFFFFFFu;
+        best = min(best, key);
+        if (inside) {
+            if (!RAGGED || d < D) atomicMin(&key_right[x - d], key);
+        } else if (active && x - d >= 0 && (!RAGGED || d < D)) {
+            atomicMin(&key_right[x - d], key);
+        }
+        if (DEBUG && active && (!RAGGED || d < D)) dbg_sum[((size_t)y * W + x) * D + d] = (uint16_t)sv;
+    }
+    return best;
+}
+
+template <int LPS, bool RAGGED, bool DEBUG>
 __global__ void __launch_bounds__(kThreads)
-    wta_kernel(const uint8_t *__restrict__ planes, int nplanes, size_t plane_elems, int W, int H,
+    wta_kernel(const uint8_t *__restrict__ planes, int nplanes, int W, int H,
                int D, int tol, uint8_t *__restrict__ disp_lr, uint8_t *__restrict__ dbg_left,
                uint8_t *__restrict__ dbg_right, uint16_t *__restrict__ dbg_sum) {
+    constexpr int G = 32 / LPS;
+    constexpr int Dp = 8 * LPS;
     extern __shared__ uint32_t smem[];
-    uint32_t *key_right = smem;                            // W keys
+    uint32_t *key_right = smem;                                // W keys
     uint8_t *dl_row = reinterpret_cast<uint8_t *>(smem + W);  // W bytes
     const int y = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = kThreads / 32;
+    const int grp = lane / LPS, li = lane % LPS;
     for (int i = threadIdx.x; i < W; i += kThreads) key_right[i] = 0xFFFFFFFFu;
     __syncthreads();
-    const int d0 = lane * DPL;
-    const bool packed = (DPL == 4) && ((D & 3) == 0);
-    for (int x = warp; x < W; x += nwarps) {
-        const size_t pix = (size_t)y * W + x;
-        uint32_t s[DPL];
+    // pixel records hold all planes of a pixel back to back: nplanes * Dp bytes
+    const size_t rec = (size_t)nplanes * Dp;
+    const uint8_t *row = planes + (size_t)y * W * rec + 8 * li;
+    const uint64_t pol = policy_evict_first();
+    // two pixel groups per iteration: 2 * nplanes loads in flight per lane
+    for (int xb = warp * 2 * G; xb < W; xb += nwarps * 2 * G) {
+        const int xa = xb + grp, xc = xb + G + grp;
+        const bool acta = xa < W, actc = xc < W;
+        const uint8_t *pa = row + (size_t)xa * rec, *pc = row + (size_t)xc * rec;
+        uint2 va[kMaxPaths], vc[kMaxPaths];
 #pragma unroll
-        for (int j = 0; j < DPL; j++) s[j] = 0;
-        if (packed) {
-            if (d0 < D) {
-                for (int p = 0; p < nplanes; p++) {
-                    const uint32_t v =
-                        *reinterpret_cast<const uint32_t *>(planes + p * plane_elems + pix * D + d0);
-#pragma unroll
-                    for (int j = 0; j < DPL; j++) s[j] += (v >> (8 * (j & 3))) & 0xFFu;
-                }
-            }
-        } else {
-            for (int p = 0; p < nplanes; p++)
-#pragma unroll
-                for (int j = 0; j < DPL; j++)
-                    if (d0 + j < D) s[j] += planes[p * plane_elems + pix * D + d0 + j];
+        for (int q = 0; q < kMaxPaths; q++) {
+            va[q] = make_uint2(0u, 0u);
+            vc[q] = make_uint2(0u, 0u);
+            if (q < nplanes && acta) va[q] = ld_plane(pa + q * Dp, pol);
+            if (q < nplanes && actc) vc[q] = ld_plane(pc + q * Dp, pol);
         }
-        uint32_t best = 0xFFFFFFFFu;
-#pragma unroll
-        for (int j = 0; j < DPL; j++) {
-            const int d = d0 + j;
-            if (d < D) {
-                const uint32_t key = (s[j] << 8) | (uint32_t)d;
-                best = min(best, key);
-                if (x - d >= 0) atomicMin(&key_right[x - d], key);
-                if (dbg_sum) dbg_sum[pix * D + d] = (uint16_t)s[j];
-            }
+        uint32_t ba = pixel_keys<LPS, RAGGED, DEBUG>(va, nplanes, acta, xa, y, W, D, li, key_right, dbg_sum);
+        uint32_t bc = pixel_keys<LPS, RAGGED, DEBUG>(vc, nplanes, actc, xc, y, W, D, li, key_right, dbg_sum);
+        ba = group_min<LPS>(ba, lane);
+        bc = group_min<LPS>(bc, lane);
+        if (li == 0) {
+            if (acta) dl_row[xa] = (uint8_t)(ba & 0xFFu);
+            if (actc) dl_row[xc] = (uint8_t)(bc & 0xFFu);
         }
-        best = __reduce_min_sync(0xffffffffu, best);
-        if (lane == 0) dl_row[x] = (uint8_t)(best & 0xFFu);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < W; x += kThreads) {
@@ -86,18 +167,32 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace
 
-cudaError_t launch_wta(const uint8_t *planes, int nplanes, size_t plane_elems, int W, int H, int D,
+cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s) {
     const size_t smem = (size_t)W * sizeof(uint32_t) + (size_t)((W + 3) & ~3);
-    if (D <= 32)
-        wta_kernel<1><<<H, kThreads, smem, s>>>(planes, nplanes, plane_elems, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum);
-    else if (D <= 64)
-        wta_kernel<2><<<H, kThreads, smem, s>>>(planes, nplanes, plane_elems, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum);
-    else if (D <= 128)
-        wta_kernel<4><<<H, kThreads, smem, s>>>(planes, nplanes, plane_elems, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum);
-    else
-        wta_kernel<8><<<H, kThreads, smem, s>>>(planes, nplanes, plane_elems, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum);
+#define SGM_WTA3(L, R, G) wta_kernel<L, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
+#define SGM_WTA(L)                              \
+    do {                                        \
+        const bool rag = D != 8 * (L);          \
+        if (dbg_sum) {                          \
+            if (rag) SGM_WTA3(L, true, true);   \
+            else SGM_WTA3(L, false, true);      \
+        } else {                                \
+            if (rag) SGM_WTA3(L, true, false);  \
+            else SGM_WTA3(L, false, false);     \
+        }                                       \
+    } while (0)
+    switch (lanes_per_scanline(D)) {
+        case 1: SGM_WTA(1); break;
+        case 2: SGM_WTA(2); break;
+        case 4: SGM_WTA(4); break;
+        case 8: SGM_WTA(8); break;
+        case 16: SGM_WTA(16); break;
+        default: SGM_WTA(32); break;
+    }
+#undef SGM_WTA3
+#undef SGM_WTA
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ SGM_PATHS_4 = 0x0F
 SGM_PATHS_8 = 0xFF
 SGM_PATHS_STREAM4 = 0x55
 
-STAGES = ("census", "aggregate", "wta_lr", "median", "uvmap")
+STAGES = ("census", "cost", "aggregate", "wta_lr", "median", "uvmap")
 
 
 class SgmError(RuntimeError):

@@ -29,8 +29,8 @@
 // never win a minimum or act as a neighbour.
 //
 // Memory.  The cost of step t + PF is loaded while step t computes (a ring of
-// PF 8-byte registers), with an L2 evict_last hint: all directions re-read
-// the volume.  Each step stores the lane's 8 path costs (8 bytes) to the
+// PF = 16 8-byte registers), with an L2 evict_last hint: all directions
+// re-read the volume; the line of step t + 32 is prefetched into L2 at step t.  Each step stores the lane's 8 path costs (8 bytes) to the
 // direction's plane, in the cost volume's byte order, with evict_first: the
 // planes are read back only once, by the WTA kernel.
 #include "sgm_internal.cuh"
@@ -59,6 +59,7 @@ PathJobs make_path_jobs(int W, int H, int D, int mask) {
 namespace {
 
 constexpr int kWarps = 4;
+constexpr int kL2Ahead = 32;  // steps between the L2 prefetch of a cost line and its use
 constexpr uint32_t kInf2 = 0x7FFF7FFFu;
 constexpr uint32_t kLo = 0x00FF00FFu;
 
@@ -92,6 +93,9 @@ __device__ __forceinline__ uint2 ld_cost(const uint2 *p, uint64_t pol) {
                  : "=r"(v.x), "=r"(v.y)
                  : "l"(p), "l"(pol));
     return v;
+}
+__device__ __forceinline__ void prefetch_l2(const uint2 *p) {
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
 }
 __device__ __forceinline__ void st_plane(uint2 *p, uint2 v, uint64_t pol) {
     asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x),
@@ -229,6 +233,12 @@ __global__ void __launch_bounds__(kWarps * 32)
         const int cstep = (dy * W + dx) * LPS;
         const int ostep = cstep * nplanes;
         int ci_ld = pix * LPS + li;  // next cost chunk to load into the ring
+        // one lane per 128-byte line of a pixel's cost record prefetches into L2
+        const bool pf_lane = ((8 * li) & 127) == 0;
+        int ci_pf = ci_ld;
+        if (pf_lane)
+            for (int i = 0; i < kL2Ahead && i < len; i++) prefetch_l2(cost + ci_pf + i * cstep);
+        ci_pf += kL2Ahead * cstep;
         int oi = (pix * nplanes + jobs.plane[k]) * LPS + li;
         uint2 ring[PF];
 #pragma unroll
@@ -245,6 +255,8 @@ __global__ void __launch_bounds__(kWarps * 32)
                 const uint2 c = ring[i];
                 if (rem > PF) ring[i] = ld_cost(cost + ci_ld, pol_keep);
                 ci_ld += cstep;
+                if (pf_lane && rem > kL2Ahead) prefetch_l2(cost + ci_pf);
+                ci_pf += cstep;
                 path_step<LPS, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
                 if (rem > 0) st_plane(planes + oi, pack_plane<RAGGED>(st), pol_stream);
                 oi += ostep;
@@ -267,7 +279,7 @@ template <int LPS>
 cudaError_t launch_lps(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                        const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
                        int blocks, cudaStream_t s) {
-    constexpr int PF = 8;  // cost loads issued 8 steps ahead
+    constexpr int PF = 16;  // cost loads issued 16 steps ahead
     const uint2 *c = reinterpret_cast<const uint2 *>(cost);
     uint2 *p = reinterpret_cast<uint2 *>(planes);
     if (D == 8 * LPS)

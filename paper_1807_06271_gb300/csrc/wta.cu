@@ -5,7 +5,7 @@
 // (all planes of a pixel back to back): LPS lanes hold a pixel's
 // disparities, 8 per lane, so a warp covers G = 32 / LPS neighbouring
 // pixels.  A lane loads its 8-byte chunk of every plane at fixed offsets
-// from one pointer (all loads issued before any use), unpacks each into four packed
+// from one pointer, one pixel group ahead of its use (register double buffer), unpacks each into four packed
 // 16-bit pairs (d+k, d+k+4) with two masks and adds them: S <= 8 * 255 fits
 // 16 bits and no half carries.  For each disparity it forms the key
 // (S << 8) | d; the left winner is the minimum key over the pixel's lanes
@@ -59,29 +59,33 @@ __device__ __forceinline__ uint2 ld_plane(const uint8_t *p, uint64_t pol) {
 
 // Sums the path planes of one pixel into four packed pairs S[k] = (S(d0+k), S(d0+k+4)),
 // folds its keys into the right-disparity slots and returns its smallest key.
+// NP > 0: NP planes (compile time); NP == 0: nplanes at run time.
 // The lane visits its 8 disparities in the order j ^ m with m = 2 * ((li >> 2) & 3),
 // which spreads the shared-memory atomics of a warp over distinct banks.
-template <int LPS, bool RAGGED, bool DEBUG>
+template <int LPS, int NP, bool RAGGED, bool DEBUG>
 __device__ __forceinline__ uint32_t pixel_keys(const uint2 (&v)[kMaxPaths], int nplanes, bool active,
                                                int x, int y, int W, int D, int li,
                                                uint32_t *key_right, uint16_t *dbg_sum) {
-    uint32_t S[4] = {0u, 0u, 0u, 0u};
+    uint32_t S0 = 0u, S1 = 0u, S2 = 0u, S3 = 0u;
 #pragma unroll
-    for (int q = 0; q < kMaxPaths; q++)
-        if (q < nplanes) {
-            S[0] += v[q].x & kLo;
-            S[1] += (v[q].x >> 8) & kLo;
-            S[2] += v[q].y & kLo;
-            S[3] += (v[q].y >> 8) & kLo;
+    for (int q = 0; q < (NP > 0 ? NP : kMaxPaths); q++)
+        if (NP > 0 || q < nplanes) {
+            S0 += v[q].x & kLo;
+            S1 += __byte_perm(v[q].x, 0u, 0x4341);
+            S2 += v[q].y & kLo;
+            S3 += __byte_perm(v[q].y, 0u, 0x4341);
         }
     const int d0 = 8 * li;
     const bool sw_reg = (li >> 2) & 1, sw_half = (li >> 3) & 1;
     const int m = (sw_reg ? 2 : 0) | (sw_half ? 4 : 0);
     uint32_t T[4];
+    T[0] = sw_reg ? S2 : S0;
+    T[1] = sw_reg ? S3 : S1;
+    T[2] = sw_reg ? S0 : S2;
+    T[3] = sw_reg ? S1 : S3;
+    if (sw_half) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const uint32_t a = sw_reg ? S[k ^ 2] : S[k];
-        T[k] = sw_half ? __byte_perm(a, a, 0x1032) : a;
+        for (int k = 0; k < 4; k++) T[k] = __byte_perm(T[k], T[k], 0x1032);
     }
     uint32_t best = 0xFFFFFFFFu;
     // every slot x - d of this lane lies in the row when x >= d0 + 7
@@ -103,13 +107,14 @@ __device__ __forceinline__ uint32_t pixel_keys(const uint2 (&v)[kMaxPaths], int 
     return best;
 }
 
-template <int LPS, bool RAGGED, bool DEBUG>
+template <int LPS, int NP, bool RAGGED, bool DEBUG>
 __global__ void __launch_bounds__(kThreads)
     wta_kernel(const uint8_t *__restrict__ planes, int nplanes, int W, int H,
                int D, int tol, uint8_t *__restrict__ disp_lr, uint8_t *__restrict__ dbg_left,
                uint8_t *__restrict__ dbg_right, uint16_t *__restrict__ dbg_sum) {
     constexpr int G = 32 / LPS;
     constexpr int Dp = 8 * LPS;
+    constexpr int NQ = NP > 0 ? NP : kMaxPaths;
     extern __shared__ uint32_t smem[];
     uint32_t *key_right = smem;                                // W keys
     uint8_t *dl_row = reinterpret_cast<uint8_t *>(smem + W);  // W bytes
@@ -119,37 +124,42 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = threadIdx.x; i < W; i += kThreads) key_right[i] = 0xFFFFFFFFu;
     __syncthreads();
     // pixel records hold all planes of a pixel back to back: nplanes * Dp bytes
-    const size_t rec = (size_t)nplanes * Dp;
+    const int np = NP > 0 ? NP : nplanes;
+    const size_t rec = (size_t)np * Dp;
     const uint8_t *row = planes + (size_t)y * W * rec + 8 * li;
     const uint64_t pol = policy_evict_first();
-    // two pixel groups per iteration: 2 * nplanes loads in flight per lane
-    for (int xb = warp * 2 * G; xb < W; xb += nwarps * 2 * G) {
-        const int xa = xb + grp, xc = xb + G + grp;
-        const bool acta = xa < W, actc = xc < W;
-        const uint8_t *pa = row + (size_t)xa * rec, *pc = row + (size_t)xc * rec;
-        uint2 va[kMaxPaths], vc[kMaxPaths];
+    const int stride = nwarps * G;
+    // software pipeline: the next pixel group's planes are loaded while the
+    // current one is reduced
+    uint2 cur[kMaxPaths], nxt[kMaxPaths];
+    int x = warp * G + grp;
 #pragma unroll
-        for (int q = 0; q < kMaxPaths; q++) {
-            va[q] = make_uint2(0u, 0u);
-            vc[q] = make_uint2(0u, 0u);
-            if (q < nplanes && acta) va[q] = ld_plane(pa + q * Dp, pol);
-            if (q < nplanes && actc) vc[q] = ld_plane(pc + q * Dp, pol);
-        }
-        uint32_t ba = pixel_keys<LPS, RAGGED, DEBUG>(va, nplanes, acta, xa, y, W, D, li, key_right, dbg_sum);
-        uint32_t bc = pixel_keys<LPS, RAGGED, DEBUG>(vc, nplanes, actc, xc, y, W, D, li, key_right, dbg_sum);
-        ba = group_min<LPS>(ba, lane);
-        bc = group_min<LPS>(bc, lane);
-        if (li == 0) {
-            if (acta) dl_row[xa] = (uint8_t)(ba & 0xFFu);
-            if (actc) dl_row[xc] = (uint8_t)(bc & 0xFFu);
-        }
+    for (int q = 0; q < kMaxPaths; q++) {
+        cur[q] = make_uint2(0u, 0u);
+        nxt[q] = make_uint2(0u, 0u);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; q++)
+        if ((NP > 0 || q < np) && x < W) cur[q] = ld_plane(row + (size_t)x * rec + q * Dp, pol);
+    for (int xb = warp * G; xb < W; xb += stride) {
+        const int xn = x + stride;
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+            if ((NP > 0 || q < np) && xn < W) nxt[q] = ld_plane(row + (size_t)xn * rec + q * Dp, pol);
+        const bool active = x < W;
+        uint32_t best = pixel_keys<LPS, NP, RAGGED, DEBUG>(cur, np, active, x, y, W, D, li, key_right, dbg_sum);
+        best = group_min<LPS>(best, lane);
+        if (li == 0 && active) dl_row[x] = (uint8_t)(best & 0xFFu);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) cur[q] = nxt[q];
+        x = xn;
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < W; x += kThreads) {
-        const int dl = dl_row[x];
+    for (int xx = threadIdx.x; xx < W; xx += kThreads) {
+        const int dl = dl_row[xx];
         uint8_t v = (uint8_t)dl;
         if (tol >= 0) {
-            const int xr = x - dl;
+            const int xr = xx - dl;
             if (xr < 0) {
                 v = SGM_INVALID;
             } else {
@@ -158,10 +168,10 @@ __global__ void __launch_bounds__(kThreads)
                 if (diff > tol) v = SGM_INVALID;
             }
         }
-        const size_t pix = (size_t)y * W + x;
+        const size_t pix = (size_t)y * W + xx;
         disp_lr[pix] = v;
         if (dbg_left) dbg_left[pix] = (uint8_t)dl;
-        if (dbg_right) dbg_right[pix] = (uint8_t)(key_right[x] & 0xFFu);
+        if (dbg_right) dbg_right[pix] = (uint8_t)(key_right[xx] & 0xFFu);
     }
 }
 
@@ -171,17 +181,23 @@ cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s) {
     const size_t smem = (size_t)W * sizeof(uint32_t) + (size_t)((W + 3) & ~3);
-#define SGM_WTA3(L, R, G) wta_kernel<L, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
-#define SGM_WTA(L)                              \
-    do {                                        \
-        const bool rag = D != 8 * (L);          \
-        if (dbg_sum) {                          \
-            if (rag) SGM_WTA3(L, true, true);   \
-            else SGM_WTA3(L, false, true);      \
-        } else {                                \
-            if (rag) SGM_WTA3(L, true, false);  \
-            else SGM_WTA3(L, false, false);     \
-        }                                       \
+#define SGM_WTA4(L, N, R, G) wta_kernel<L, N, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
+#define SGM_WTA(L)                                       \
+    do {                                                 \
+        const bool rag = D != 8 * (L);                   \
+        if (dbg_sum) {                                   \
+            if (rag) SGM_WTA4(L, 0, true, true);         \
+            else SGM_WTA4(L, 0, false, true);            \
+        } else if (nplanes == 8) {                       \
+            if (rag) SGM_WTA4(L, 8, true, false);        \
+            else SGM_WTA4(L, 8, false, false);           \
+        } else if (nplanes == 4) {                       \
+            if (rag) SGM_WTA4(L, 4, true, false);        \
+            else SGM_WTA4(L, 4, false, false);           \
+        } else {                                         \
+            if (rag) SGM_WTA4(L, 0, true, false);        \
+            else SGM_WTA4(L, 0, false, false);           \
+        }                                                \
     } while (0)
     switch (lanes_per_scanline(D)) {
         case 1: SGM_WTA(1); break;
@@ -191,7 +207,7 @@ cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
         case 16: SGM_WTA(16); break;
         default: SGM_WTA(32); break;
     }
-#undef SGM_WTA3
+#undef SGM_WTA4
 #undef SGM_WTA
     return cudaGetLastError();
 }

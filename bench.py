@@ -333,7 +333,8 @@ def run_ours(args, w, windex):
         cpu = {"value": de_cpu / dt / 1e6, "unit": "MDE/s", "cores": 1, "kind": "oracle",
                "sample": f"{reps} full {w.W}x{w.H} pair(s), single thread, {dt:.1f} s"}
 
-    launches_per_step = 4 + (2 if w.uv else 0)
+    # census, cost, aggregate, wta_lr, median (a device copy when off), U/V
+    launches_per_step = 4 + (1 if w.median_k > 1 else 0) + (1 if w.uv else 0)
     if rank == 0:
         line = {
             "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": world,
@@ -361,6 +362,106 @@ def run_ours(args, w, windex):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# extra modes: batched pairs and continuous serving (not the headline line)
+# ---------------------------------------------------------------------------
+
+def batch_specs(n=64, seed=1807 + 3):
+    rng = scenes.Rng(seed)
+    sizes = [(320, 240), (640, 480), (1242, 375), (1280, 720)]
+    si = rng.integers(0, 3, n)
+    di = rng.integers(0, 1, n)
+    return [(sizes[a][0], sizes[a][1], (64, 128)[b]) for a, b in zip(si, di)]
+
+
+def run_batch(args):
+    """64 pairs of mixed size and disparity range (9x7 census, 8 paths,
+    P1=8, P2=96, LR 1, 3x3 median, U/V maps): one graph-replayed batch call per
+    step, against the same pairs launched one after another."""
+    import torch
+
+    from paper_1807_06271_gb300 import sgm
+    torch.cuda.set_device(0)
+    specs = batch_specs()
+    p = sgm.SgmParams(census_w=9, census_h=7, path_mask=0xFF, P1=8, P2=96, lr_tolerance=1, median_k=3)
+    hs, L, R, Dd, U, V = [], [], [], [], [], []
+    for i, (W, H, D) in enumerate(specs):
+        sc = scenes.ground_scene(W, H, D, seed=1807 + 3 + i, n_obstacles=3, dlo=D // 6, dhi=(D * 6) // 7,
+                                 texture="value", sigma=2.0, occlusion=0.05)
+        hs.append(sgm.Handle(W, H, D, p))
+        L.append(torch.from_numpy(sc.left).cuda())
+        R.append(torch.from_numpy(sc.right).cuda())
+        Dd.append(torch.empty((H, W), dtype=torch.uint8, device="cuda"))
+        U.append(torch.empty((D, W), dtype=torch.int16, device="cuda"))
+        V.append(torch.empty((H, D), dtype=torch.int16, device="cuda"))
+    tuned = {}
+    for i, (W, H, D) in enumerate(specs):
+        if (W, H, D) not in tuned:
+            tuned[(W, H, D)] = sgm.sgm_autotune(hs[i], L[i], R[i], Dd[i])
+    for i, (W, H, D) in enumerate(specs):  # handles made before tuning pick it up here
+        hs[i].close()
+        hs[i] = sgm.Handle(W, H, D, p)
+    de = sum(W * H * D for W, H, D in specs)
+    st = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    batch_ms = timed(lambda: sgm.sgm_batch_compute(hs, L, R, Dd, U, V, st), args.steps)
+
+    def one_by_one():
+        for i in range(len(specs)):
+            hs[i].compute(L[i], R[i], Dd[i], st)
+            hs[i].uvmap(Dd[i], U[i], V[i], st)
+    seq_ms = timed(one_by_one, max(1, args.steps // 4))
+    line = {"metric": "MDE/s", "value": de / (batch_ms / 1e3) / 1e6, "unit": "MDE/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(specs),
+                       "de_per_step": de, "tuned_blocks_per_sm": {f"{k[0]}x{k[1]}d{k[2]}": v for k, v in tuned.items()}},
+            "one_pair_per_launch": {"ms_per_step": seq_ms, "value": de / (seq_ms / 1e3) / 1e6}}
+    print(json.dumps(line), flush=True)
+    for h in hs:
+        h.close()
+    return 0
+
+
+def run_serve(args):
+    """8 cameras (4 x 640x480 D=64, 4 x 1280x720 D=128) with Poisson arrivals
+    at 30 fps each, full path + U/V per frame, 4 GB device-memory budget."""
+    import torch
+
+    from paper_1807_06271_gb300 import serving
+    torch.cuda.set_device(0)
+    specs = serving.camera_streams()
+    frames = serving.stream_frames(specs, per_stream=4)
+    ex = serving.CudaExecutor(specs, frames)
+    sch = serving.Scheduler(specs, ex, memory_budget=4 << 30)
+    warm = serving.poisson_schedule(specs, duration_s=0.5, seed=1)
+    serving.Scheduler(specs, ex, memory_budget=4 << 30).run(warm, speed=1.0)  # allocates slots, warms up
+    st = sch.run(serving.poisson_schedule(specs, duration_s=args.serve_seconds, seed=1807 + 4))
+    sm = st.summary()
+    line = {"metric": "p99 latency", "value": sm["p99_ms"], "unit": "ms", "n_gpus": 1,
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "serve-8cams-30fps-4GB", "seconds": args.serve_seconds},
+            "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "max_ms": sm["max_ms"],
+            "frames": sm["frames"], "mde_per_s": sm["mde_per_s"], "slots": sm["slots"],
+            "device_bytes": sm["device_bytes"], "max_queue": sm["max_queue"]}
+    print(json.dumps(line), flush=True)
+    ex.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,9 +472,17 @@ def main(argv=None):
                     choices=sorted(WORKLOAD_INDEX))
     ap.add_argument("--cpu-frames", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["frame", "batch", "serve"], default="frame",
+                    help="frame: the headline single-pair line; batch: 64 mixed pairs per step; "
+                         "serve: 8 Poisson camera streams")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     w = scenes.WORKLOADS[args.workload]
     windex = WORKLOAD_INDEX[args.workload]
     if args.impl == "reference":

@@ -100,12 +100,25 @@ int sgm_compute_host(sgm_handle h, const uint8_t *left, const uint8_t *right,
 
 /* Many pairs in one go (the method of Sec. 3.1 per pair): n handles (each
  * with its own size and parameters), device pointers left[i], right[i],
- * disp[i] and optional umap[i]/vmap[i] (NULL = skip maps for pair i).  The
- * pairs run concurrently on internal streams forked from and joined back to
- * `stream`.  Handles must be distinct. */
+ * disp[i] and optional umap[i]/vmap[i] (umap/vmap NULL, or NULL entries, skip
+ * the maps of a pair).  Every pair's pipeline runs on its own branch of one
+ * CUDA graph, forked from and joined back to `stream`; the graph is captured
+ * on the first call and replayed while the same handles and buffers (and
+ * tuning) come back, up to 8 distinct batches per process (least recently
+ * used dropped first).  Destroying a handle drops the graphs that use it.
+ * With stage timing enabled on any handle the pairs are launched directly on
+ * forked streams instead.  Handles must be distinct. */
 int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
                       const uint8_t *const *right, uint8_t *const *disp,
                       uint16_t *const *umap, uint16_t *const *vmap, void *stream);
+
+/* Autotuner: times the pipeline on this pair (device pointers as for
+ * sgm_compute; disp is overwritten) with 1, 2, 3, 4 and 6 resident blocks per
+ * SM for the aggregation kernel and keeps the fastest for h and for handles
+ * created later in this process with the same W, H, D, path mask, census
+ * window and P2.  Synchronises `stream`.  *best_blocks_per_sm may be NULL. */
+int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                 void *stream, int *best_blocks_per_sm);
 
 /* Short English text for a status code (static storage). */
 const char *sgm_status_string(int status);

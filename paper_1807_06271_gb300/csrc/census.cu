@@ -15,38 +15,58 @@ namespace sgm {
 namespace {
 
 constexpr int kBX = 32, kBY = 8;
+constexpr int kRows = 4;  // rows per thread of the unrolled census kernel
 
+// One CTA covers 32 x 32 pixels of one image; a thread computes 4 pixels of
+// one column.  The tile plus halo is staged as bytes with 255 for "outside
+// the image": 255 is never darker than a centre pixel, which gives the 0 bit
+// the border rule asks for.  Each bit is the sign of I(q) - I(p), shifted
+// into one of two 32-bit halves (two instructions per bit).
 template <typename CodeT, int CW, int CH>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
                   int W, int H, CodeT *__restrict__ codes) {
-    constexpr int TW = kBX + CW - 1, TH = kBY + CH - 1;
+    constexpr int TW = kBX + CW - 1, TH = kBY * kRows + CH - 1;
     constexpr int RX = CW / 2, RY = CH / 2;
-    __shared__ uint16_t tile[TH][TW];
+    __shared__ uint8_t tile[TH][TW];
     const uint8_t *img = blockIdx.z ? right : left;
-    const int x0 = blockIdx.x * kBX - RX, y0 = blockIdx.y * kBY - RY;
+    const int x0 = blockIdx.x * kBX - RX, y0 = blockIdx.y * kBY * kRows - RY;
     const int tid = threadIdx.y * kBX + threadIdx.x;
     for (int i = tid; i < TW * TH; i += kBX * kBY) {
-        int ty = i / TW, tx = i - ty * TW;
-        int gx = x0 + tx, gy = y0 + ty;
-        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * pitch + gx] : 256;
+        const int ty = i / TW, tx = i - ty * TW;
+        const int gx = x0 + tx, gy = y0 + ty;
+        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * pitch + gx] : 255;
     }
     __syncthreads();
-    const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const uint16_t c = tile[threadIdx.y + RY][threadIdx.x + RX];
-    CodeT code = 0;
-    int bit = 0;
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    if (x >= W) return;
 #pragma unroll
-    for (int wy = 0; wy < CH; wy++) {
+    for (int r = 0; r < kRows; r++) {
+        const int ly = threadIdx.y + kBY * r;
+        const int y = blockIdx.y * kBY * kRows + ly;
+        if (y >= H) break;
+        const int c = tile[ly + RY][threadIdx.x + RX];
+        // I(q) - I(p) is negative exactly when q is darker; a funnel shift
+        // appends its sign bit.  Walking the window backwards leaves the
+        // first neighbour (raster order) at bit 0.
+        uint32_t lo = 0, hi = 0;
+        int bit = CW * CH - 2;
 #pragma unroll
-        for (int wx = 0; wx < CW; wx++) {
-            if (wy == RY && wx == RX) continue;
-            code |= (CodeT)(tile[threadIdx.y + wy][threadIdx.x + wx] < c) << bit;
-            bit++;
+        for (int wy = CH - 1; wy >= 0; wy--) {
+#pragma unroll
+            for (int wx = CW - 1; wx >= 0; wx--) {
+                if (wy == RY && wx == RX) continue;
+                const uint32_t diff = (uint32_t)((int)tile[ly + wy][threadIdx.x + wx] - c);
+                if (bit >= 32) hi = __funnelshift_l(diff, hi, 1);
+                else lo = __funnelshift_l(diff, lo, 1);
+                bit--;
+            }
         }
+        CodeT code;
+        if constexpr (sizeof(CodeT) == 8) code = ((uint64_t)hi << 32) | lo;
+        else code = lo;
+        codes[(size_t)blockIdx.z * W * H + (size_t)y * W + x] = code;
     }
-    codes[(size_t)blockIdx.z * W * H + (size_t)y * W + x] = code;
 }
 
 // Generic window (any odd size up to 64 bits), loops not unrolled.
@@ -84,10 +104,10 @@ __global__ void __launch_bounds__(kBX *kBY)
 // Matching cost volume (Eq. 1): C(x,y,d) = popc(code_l(x,y) ^ code_r(x-d,y)),
 // or the code width when x-d < 0, for d < D; padding slots d >= D hold the
 // code width too.  One CTA per segment of kSeg pixels of one row: the
-// segment's left codes and the right codes it reaches (kSeg + Dp - 1 of them)
-// are staged in shared memory.  A thread computes one 8-disparity chunk of one
-// pixel, with consecutive threads on consecutive pixels so that the
-// shared-memory code reads are conflict-free; the segment is transposed
+// segment's left codes and the right codes it reaches (kSeg + Dp + 2 of them)
+// are staged in shared memory.  A thread computes one 8-disparity chunk of two
+// neighbouring pixels from 9 consecutive right codes read as aligned vectors,
+// with consecutive threads on consecutive pixel pairs (conflict-free reads); the segment is transposed
 // through a padded shared tile and written out with coalesced 8-byte stores
 // (the segment's Dp-byte pixel records are contiguous in global memory).
 // popc runs on the XU pipe (16 per SM per clock; two per estimate for 64-bit
@@ -104,41 +124,83 @@ __global__ void __launch_bounds__(kCostThreads)
     cost_kernel(const CodeT *__restrict__ codes, int W, int H, int D, int Dp, int nbits,
                 uint8_t *__restrict__ cost) {
     extern __shared__ __align__(16) unsigned char cost_smem[];
-    const int stride = Dp + 8;  // padded tile row (bytes): conflict-free 8-byte tile writes
-    uint8_t *tile = cost_smem;                                         // [kSeg][stride]
-    CodeT *cl = reinterpret_cast<CodeT *>(cost_smem + kSeg * stride);  // [kSeg]
-    CodeT *cr = cl + kSeg;                                             // [kSeg + Dp - 1]
+    const int stride = Dp + 8;  // padded tile row (bytes)
+    uint8_t *tile = cost_smem;                                          // [kSeg][stride]
+    const int tile_bytes = (kSeg * stride + 15) & ~15;
+    CodeT *cl = reinterpret_cast<CodeT *>(cost_smem + tile_bytes);     // [kSeg]
+    CodeT *cr = cl + kSeg;                                              // [kSeg + Dp + 2]
     const int y = blockIdx.y, x0 = blockIdx.x * kSeg;
-    const int xr0 = x0 - (Dp - 1);  // right code cr[i] is column xr0 + i
+    const int xr0 = x0 - Dp - 1;  // right code cr[i] is column xr0 + i
     const CodeT *rowl = codes + (size_t)y * W;
     const CodeT *rowr = codes + (size_t)W * H + (size_t)y * W;
     for (int i = threadIdx.x; i < kSeg; i += kCostThreads) cl[i] = x0 + i < W ? rowl[x0 + i] : 0;
-    for (int i = threadIdx.x; i < kSeg + Dp - 1; i += kCostThreads) {
+    for (int i = threadIdx.x; i < kSeg + Dp + 2; i += kCostThreads) {
         const int xr = xr0 + i;
         cr[i] = (xr >= 0 && xr < W) ? rowr[xr] : 0;
     }
     __syncthreads();
     const int chunks = Dp / 8;
     const bool border = x0 < Dp;  // only the first segments see x - d < 0
-    for (int it = threadIdx.x; it < kSeg * chunks; it += kCostThreads) {
-        const int px = it % kSeg, i = it / kSeg;
-        const int x = x0 + px;
-        const CodeT a = cl[px];
-        const CodeT *r = cr + px + Dp - 1 - 8 * i;  // right column x - d sits at r[-(d - 8i)]
-        uint32_t c[8];
+    // A thread takes one 8-disparity chunk of the pixel pair (px, px+1), px even.
+    // Column x - d of pixel px sits at cr[px - d + Dp + 1]: for the chunk's
+    // disparities 8i+j the pair needs the 9 codes w[k] = cr[s + k], s = px + Dp - 8i - 6
+    // (even, so the run is 16-byte aligned for 8-byte codes): pixel px uses
+    // w[7 - j], pixel px + 1 uses w[8 - j].
+    for (int it = threadIdx.x; it < (kSeg / 2) * chunks; it += kCostThreads) {
+        const int pr = it % (kSeg / 2), i = it / (kSeg / 2);
+        const int px = 2 * pr;
+        const int sidx = px + Dp - 8 * i - 6;
+        CodeT w[9];
+        if constexpr (sizeof(CodeT) == 8) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) c[j] = popcnt(a ^ r[-j]);
+            for (int k = 0; k < 4; k++) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cr + sidx + 2 * k);
+                w[2 * k] = v.x;
+                w[2 * k + 1] = v.y;
+            }
+            w[8] = cr[sidx + 8];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint2 v = *reinterpret_cast<const uint2 *>(cr + sidx + 2 * k);
+                w[2 * k] = v.x;
+                w[2 * k + 1] = v.y;
+            }
+            w[8] = cr[sidx + 8];
+        }
+        CodeT a0, a1;
+        if constexpr (sizeof(CodeT) == 8) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cl + px);
+            a0 = v.x;
+            a1 = v.y;
+        } else {
+            const uint2 v = *reinterpret_cast<const uint2 *>(cl + px);
+            a0 = v.x;
+            a1 = v.y;
+        }
+        uint32_t c[8], e[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            c[j] = popcnt(a0 ^ w[7 - j]);
+            e[j] = popcnt(a1 ^ w[8 - j]);
+        }
         if (RAGGED || border) {
+            const int x = x0 + px;
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const int d = 8 * i + j;
                 if ((RAGGED && d >= D) || x - d < 0) c[j] = (uint32_t)nbits;
+                if ((RAGGED && d >= D) || x + 1 - d < 0) e[j] = (uint32_t)nbits;
             }
         }
-        uint2 v;
-        v.x = c[0] | (c[1] << 8) | (c[4] << 16) | (c[5] << 24);
-        v.y = c[2] | (c[3] << 8) | (c[6] << 16) | (c[7] << 24);
-        *reinterpret_cast<uint2 *>(tile + px * stride + 8 * i) = v;
+        // byte order of a chunk: d+0 d+1 d+4 d+5 | d+2 d+3 d+6 d+7
+        uint2 vc, ve;
+        vc.x = (c[5] * 256u + c[4]) * 65536u + (c[1] * 256u + c[0]);
+        vc.y = (c[7] * 256u + c[6]) * 65536u + (c[3] * 256u + c[2]);
+        ve.x = (e[5] * 256u + e[4]) * 65536u + (e[1] * 256u + e[0]);
+        ve.y = (e[7] * 256u + e[6]) * 65536u + (e[3] * 256u + e[2]);
+        *reinterpret_cast<uint2 *>(tile + px * stride + 8 * i) = vc;
+        *reinterpret_cast<uint2 *>(tile + (px + 1) * stride + 8 * i) = ve;
     }
     __syncthreads();
     const int npx = min(kSeg, W - x0);
@@ -155,10 +217,11 @@ __global__ void __launch_bounds__(kCostThreads)
 cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
                           int cw, int ch, int code_bytes, void *codes, cudaStream_t s) {
     dim3 block(kBX, kBY), grid((W + kBX - 1) / kBX, (H + kBY - 1) / kBY, 2);
+    const dim3 grid4((W + kBX - 1) / kBX, (H + kBY * kRows - 1) / (kBY * kRows), 2);
     if (cw == 5 && ch == 5 && code_bytes == 4)
-        census_kernel<uint32_t, 5, 5><<<grid, block, 0, s>>>(left, right, pitch, W, H, (uint32_t *)codes);
+        census_kernel<uint32_t, 5, 5><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (uint32_t *)codes);
     else if (cw == 9 && ch == 7 && code_bytes == 8)
-        census_kernel<uint64_t, 9, 7><<<grid, block, 0, s>>>(left, right, pitch, W, H, (uint64_t *)codes);
+        census_kernel<uint64_t, 9, 7><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (uint64_t *)codes);
     else {
         size_t smem = (size_t)(kBX + cw - 1) * (kBY + ch - 1) * sizeof(uint16_t);
         if (code_bytes == 4)
@@ -176,7 +239,7 @@ namespace sgm {
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
                         uint8_t *cost, cudaStream_t s) {
     const int Dp = padded_disparities(D);
-    const size_t smem = (size_t)kSeg * (Dp + 8) + (size_t)(2 * kSeg + Dp - 1) * code_bytes;
+    const size_t smem = (((size_t)kSeg * (Dp + 8) + 15) & ~(size_t)15) + (size_t)(2 * kSeg + Dp + 2) * code_bytes;
     const dim3 grid((W + kSeg - 1) / kSeg, H);
     cudaError_t e;
     const bool rag = D != Dp;

@@ -72,46 +72,50 @@ __global__ void __launch_bounds__(kMX *kMY)
 }
 
 // ---------------------------------------------------------------------------
-// V-map: one CTA per row, shared-memory histogram of D bins.
-// U-map: one CTA per strip of 32 columns; a thread owns one column of one
-// row phase and bumps a shared-memory histogram [D][32] with atomics.
-// Every output element is written exactly once, so no clearing is needed.
+// U- and V-maps in one launch of 1024-thread CTAs.  The first ceil(W/32)
+// CTAs build the U-map of a 32-column strip: 32 row phases x 32 columns walk
+// the strip and bump a shared [D][32] histogram; each column's counts are
+// then written once.  The remaining CTAs build the V-map of 8 rows each with
+// shared [8][D] histograms.  Every output element is written exactly once,
+// so no clearing is needed.
 // ---------------------------------------------------------------------------
 
-constexpr int kUVThreads = 256;
+constexpr int kUVThreads = 1024, kVRows = 8;
 
 __global__ void __launch_bounds__(kUVThreads)
-    vmap_kernel(const uint8_t *__restrict__ disp, int W, int D, uint16_t *__restrict__ vmap) {
+    uvmap_kernel(const uint8_t *__restrict__ disp, int W, int H, int D, int ustrips,
+                 uint16_t *__restrict__ umap, uint16_t *__restrict__ vmap) {
     extern __shared__ uint32_t hist[];
-    const int y = blockIdx.x;
-    for (int d = threadIdx.x; d < D; d += kUVThreads) hist[d] = 0;
-    __syncthreads();
-    for (int x = threadIdx.x; x < W; x += kUVThreads) {
-        const int d = disp[(size_t)y * W + x];
-        if (d < D) atomicAdd(&hist[d], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < D; d += kUVThreads) vmap[(size_t)y * D + d] = (uint16_t)hist[d];
-}
-
-__global__ void __launch_bounds__(kUVThreads)
-    umap_kernel(const uint8_t *__restrict__ disp, int W, int H, int D, uint16_t *__restrict__ umap) {
-    extern __shared__ uint32_t hist[];  // [D][32]
-    const int x0 = blockIdx.x * 32;
-    const int col = threadIdx.x & 31, phase = threadIdx.x >> 5, nphase = kUVThreads / 32;
-    for (int i = threadIdx.x; i < D * 32; i += kUVThreads) hist[i] = 0;
-    __syncthreads();
-    const int x = x0 + col;
-    if (x < W) {
-        for (int y = phase; y < H; y += nphase) {
-            const int d = disp[(size_t)y * W + x];
-            if (d < D) atomicAdd(&hist[d * 32 + col], 1u);
+    if ((int)blockIdx.x < ustrips) {
+        const int x0 = blockIdx.x * 32;
+        const int col = threadIdx.x & 31, phase = threadIdx.x >> 5, nphase = kUVThreads / 32;
+        for (int i = threadIdx.x; i < D * 32; i += kUVThreads) hist[i] = 0;
+        __syncthreads();
+        const int x = x0 + col;
+        if (x < W) {
+            for (int y = phase; y < H; y += nphase) {
+                const int d = disp[(size_t)y * W + x];
+                if (d < D) atomicAdd(&hist[d * 32 + col], 1u);
+            }
         }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < D * 32; i += kUVThreads) {
-        const int d = i >> 5, c = i & 31;
-        if (x0 + c < W) umap[(size_t)d * W + x0 + c] = (uint16_t)hist[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < D * 32; i += kUVThreads) {
+            const int d = i >> 5, c = i & 31;
+            if (x0 + c < W) umap[(size_t)d * W + x0 + c] = (uint16_t)hist[i];
+        }
+    } else {
+        const int y0 = ((int)blockIdx.x - ustrips) * kVRows;
+        for (int i = threadIdx.x; i < kVRows * D; i += kUVThreads) hist[i] = 0;
+        __syncthreads();
+        const int rows = min(kVRows, H - y0);
+        for (int i = threadIdx.x; i < rows * W; i += kUVThreads) {
+            const int r = i / W, x = i - r * W;
+            const int d = disp[(size_t)(y0 + r) * W + x];
+            if (d < D) atomicAdd(&hist[r * D + d], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < rows * D; i += kUVThreads)
+            vmap[(size_t)y0 * D + i] = (uint16_t)hist[i];
     }
 }
 
@@ -130,10 +134,9 @@ cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, 
 
 cudaError_t launch_uvmap(const uint8_t *disp, int W, int H, int D, uint16_t *umap, uint16_t *vmap,
                          cudaStream_t s) {
-    vmap_kernel<<<H, kUVThreads, D * sizeof(uint32_t), s>>>(disp, W, D, vmap);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    umap_kernel<<<(W + 31) / 32, kUVThreads, (size_t)D * 32 * sizeof(uint32_t), s>>>(disp, W, H, D, umap);
+    const int ustrips = (W + 31) / 32, vblocks = (H + kVRows - 1) / kVRows;
+    const size_t smem = (size_t)(D * 32 > kVRows * D ? D * 32 : kVRows * D) * sizeof(uint32_t);
+    uvmap_kernel<<<ustrips + vblocks, kUVThreads, smem, s>>>(disp, W, H, D, ustrips, umap, vmap);
     return cudaGetLastError();
 }
 

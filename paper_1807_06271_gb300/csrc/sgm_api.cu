@@ -186,6 +186,15 @@ int dev_alloc(T **p, size_t bytes) {
 
 }  // namespace
 
+// One pair (and its maps when umap/vmap are non-null) on stream s; used by
+// the batched entry points in batch.cu.
+int sgm::compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                      uint16_t *umap, uint16_t *vmap, cudaStream_t s) {
+    int rc = compute_on(h, left, right, disp, s);
+    if (rc == SGM_OK && umap && vmap) rc = uv_on(h, disp, umap, vmap, s);
+    return rc;
+}
+
 // Same host-side argument checks as sgm_create, for entry points without a handle.
 int sgm::validate_params(int W, int H, int D, const sgm_params *p) { return validate(W, H, D, p); }
 
@@ -227,6 +236,8 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
         if ((params->path_mask >> r) & 1) h->path_of_plane[h->npaths++] = r;
     h->Dp = padded_disparities(D);
     h->agg_blocks_per_sm = 2;  // 8 resident warps per SM
+    const int tuned = tuned_blocks_per_sm(h);
+    if (tuned > 0) h->agg_blocks_per_sm = tuned;
     if (const char *env = getenv("SGM_AGG_BLOCKS_PER_SM")) {  // tuning override
         const int v = atoi(env);
         if (v >= 1 && v <= 16) h->agg_blocks_per_sm = v;
@@ -255,6 +266,7 @@ int sgm_destroy(sgm_handle h) {
     if (!h) return SGM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
+    batch_forget(h);
     free_handle(h);
     return SGM_OK;
 }
@@ -325,42 +337,6 @@ int sgm_compute_host(sgm_handle h, const uint8_t *left, const uint8_t *right, ui
             rc = SGM_ERR_CUDA;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == SGM_OK) rc = SGM_ERR_CUDA;
-    return rc;
-}
-
-int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
-                      const uint8_t *const *right, uint8_t *const *disp, uint16_t *const *umap,
-                      uint16_t *const *vmap, void *stream) {
-    if (n < 0 || (n > 0 && (!hs || !left || !right || !disp))) return SGM_ERR_INVALID_ARG;
-    for (int i = 0; i < n; i++) {
-        if (!hs[i] || !left[i] || !right[i] || !disp[i]) return SGM_ERR_INVALID_ARG;
-        if (umap && vmap && ((!umap[i]) != (!vmap[i]))) return SGM_ERR_INVALID_ARG;
-        for (int j = 0; j < i; j++)
-            if (hs[j] == hs[i]) return SGM_ERR_INVALID_ARG;
-    }
-    if (n == 0) return SGM_OK;
-    DeviceGuard g(hs[0]->device);
-    if (!g.ok) return SGM_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    int rc = SGM_OK;
-    for (int i = 0; i < n && rc == SGM_OK; i++) {
-        sgm_handle_s *h = hs[i];
-        if (h->device != hs[0]->device) return SGM_ERR_INVALID_ARG;
-        if (cudaEventRecord(h->fork_ev, s) != cudaSuccess ||
-            cudaStreamWaitEvent(h->side, h->fork_ev, 0) != cudaSuccess) {
-            rc = SGM_ERR_CUDA;
-            break;
-        }
-        rc = compute_on(h, left[i], right[i], disp[i], h->side);
-        if (rc == SGM_OK && umap && umap[i]) rc = uv_on(h, disp[i], umap[i], vmap[i], h->side);
-    }
-    // Join every side stream that was forked, whatever happened.
-    for (int i = 0; i < n; i++) {
-        sgm_handle_s *h = hs[i];
-        if (cudaEventRecord(h->join_ev, h->side) != cudaSuccess ||
-            cudaStreamWaitEvent(s, h->join_ev, 0) != cudaSuccess)
-            rc = rc == SGM_OK ? SGM_ERR_CUDA : rc;
-    }
     return rc;
 }
 

@@ -122,6 +122,14 @@ cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s);
 cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, cudaStream_t s);
+// One pair (and its U/V maps when umap and vmap are non-null) on stream s.
+int compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                 uint16_t *umap, uint16_t *vmap, cudaStream_t s);
+// Drops cached batch graphs that use h (called before h is freed).
+void batch_forget(sgm_handle_s *h);
+// Aggregation blocks per SM chosen by sgm_autotune for h's shape, or 0.
+int tuned_blocks_per_sm(const sgm_handle_s *h);
+
 // Host-side argument checks shared by every entry point (SGM_OK or an error status).
 int validate_params(int W, int H, int D, const sgm_params *p);
 

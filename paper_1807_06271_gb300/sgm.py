@@ -76,6 +76,7 @@ _SIGNATURES = {
     "sgm_set_timing": [_P, _I],
     "sgm_get_stage_times": [_P, _P, _P, _I, _P],
     "sgm_compute_static": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P, _P],
+    "sgm_autotune": [_P, _P, _P, _P, _P, _P],
 }
 
 SGM_STATIC_SCRATCH_BYTES = 32 << 20
@@ -246,6 +247,18 @@ def sgm_batch_compute(handles, lefts, rights, disps, umaps=None, vmaps=None, str
         V = arr(_P, [_dev(t, ("uint16", "int16"), (h.H, h.D), "vmap") if t is not None else None
                      for h, t in zip(handles, vmaps)])
     _check(load().sgm_batch_compute(n, hs, L, R, Dd, U, V, _stream(stream)), "sgm_batch_compute")
+
+
+def sgm_autotune(h: Handle, left, right, disp, stream=None) -> int:
+    """Pick the aggregation kernel's resident blocks per SM for h's shape by
+    timing the pipeline on this pair; returns the chosen value."""
+    shp = h._img_shape()
+    best = _I()
+    _check(load().sgm_autotune(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
+        _dev(disp, ("uint8",), (h.H, h.W), "disp"), _stream(stream), ctypes.byref(best)),
+        "sgm_autotune")
+    return best.value
 
 
 def sgm_get_shape(h: Handle):

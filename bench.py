@@ -325,6 +325,36 @@ def run_ours(args, w, windex):
            "d2h_bytes_per_step": w.W * w.H + (2 * w.D * w.W + 2 * w.H * w.D if w.uv else 0),
            "steps": e2e_steps, "api": "sgm_compute_host"}
 
+    # next rows, timed after the headline loop: map post-processing (Sec. 3.2)
+    # and the pipeline reading its inputs through identity rectification maps
+    # (Sec. 3.1.1)
+    extras = {}
+    if w.uv:
+        uo = torch.empty((w.D, w.W), dtype=torch.uint8, device="cuda")
+        vo = torch.empty((w.H, w.D), dtype=torch.uint8, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sgm.uvmap_postprocess(h, umap, vmap, 3, 6, None, None, 1, uo, vo, stream)
+        e0.record(stream)
+        for _ in range(50):
+            sgm.uvmap_postprocess(h, umap, vmap, 3, 6, None, None, 1, uo, vo, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extras["uv_postprocess_us"] = e0.elapsed_time(e1) / 50 * 1e3
+    yy, xx = np.mgrid[0:w.H, 0:w.W]
+    mx = torch.from_numpy(xx.astype(np.int16)).cuda()
+    my = torch.from_numpy(yy.astype(np.int16)).cuda()
+    sgm.sgm_set_rectification(h, mx, my, mx, my)
+    for _ in range(3):
+        h.compute(left, right, disp, stream)
+    sgm.sgm_set_timing(h, True)
+    sgm.sgm_get_stage_times(h)
+    for _ in range(50):
+        h.compute(left, right, disp, stream)
+    rect_stage = sgm.sgm_get_stage_times(h)
+    sgm.sgm_set_timing(h, False)
+    sgm.sgm_set_rectification(h)
+    extras["census_rectified_us"] = rect_stage["census"][0] / max(rect_stage["census"][1], 1) * 1e3
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = w.H
@@ -353,6 +383,7 @@ def run_ours(args, w, windex):
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,
             "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stage.items() if v[1]},
+            "next_rows": extras,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

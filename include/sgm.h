@@ -91,6 +91,28 @@ int sgm_compute(sgm_handle h, const uint8_t *left, const uint8_t *right,
 int uvmap_compute(sgm_handle h, const uint8_t *disp, uint16_t *umap,
                   uint16_t *vmap, void *stream);
 
+/* Post-processing of the maps before obstacle extraction (Sec. 3.2; the
+ * paper names the steps but not their parameters):
+ *   binary(i,j) = map(i,j) >= threshold inside the region of interest
+ *                 [roi[0], roi[1]) x [roi[2], roi[3]) (rows x columns of the
+ *                 map), 0 outside it;
+ *   dilated     = max of binary over a (2 dilate_r + 1)^2 square;
+ *   out         = 3x3 binomial Gaussian [1 2 1; 2 4 2; 1 2 1]/16 of
+ *                 255 * dilated, (sum + 8) / 16;
+ * cells outside the map count as 0.  The U-map is D x W (rows d, columns x),
+ * the V-map H x D (rows y, columns d). */
+typedef struct sgm_uv_post {
+    int u_threshold, v_threshold;
+    int u_roi[4]; /* d0, d1, x0, x1 */
+    int v_roi[4]; /* y0, y1, d0, d1 */
+    int dilate_r; /* 0..7 */
+} sgm_uv_post;
+
+/* umap/vmap: device maps from uvmap_compute; uout (D x W) and vout (H x D):
+ * device uint8 outputs, either may be NULL to skip that map. */
+int uvmap_postprocess(sgm_handle h, const uint16_t *umap, const uint16_t *vmap,
+                      const sgm_uv_post *params, uint8_t *uout, uint8_t *vout, void *stream);
+
 /* sgm_compute followed by uvmap_compute with HOST buffers: copies left/right
  * (H x W each, dense) to handle-owned device buffers, runs both, copies disp
  * (H x W) and, when non-NULL, umap (D x W) and vmap (H x D) back, and waits
@@ -125,6 +147,16 @@ const char *sgm_status_string(int status);
 
 /* Sizes the handle was created with; any pointer may be NULL. */
 int sgm_get_shape(sgm_handle h, int *W, int *H, int *D, int *census_bits);
+
+/* Rectification (Sec. 3.1.1): later calls on h read the left and right
+ * images through integer maps, I_rect(x, y) = I(map_x(x, y), map_y(x, y)),
+ * inside the census kernel's tile load.  Each map is a device W x H uint16
+ * array owned by the caller, which keeps it alive and unchanged while h uses
+ * it; a pixel whose map entry is >= W (x) or >= H (y) reads as 0.  Pass four
+ * NULLs to switch rectification off (the default); 1 to 3 NULLs is
+ * SGM_ERR_INVALID_ARG.  sgm_compute_static never rectifies. */
+int sgm_set_rectification(sgm_handle h, const uint16_t *left_x, const uint16_t *left_y,
+                          const uint16_t *right_x, const uint16_t *right_y);
 
 /* ---- per-stage parity access (same kernels as sgm_compute) --------------- */
 

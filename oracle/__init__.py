@@ -61,11 +61,13 @@ def _load():
         lib.oracle_median.argtypes = [P, I, I, I, P]
         lib.oracle_uvmap.argtypes = [P, I, I, I, P, P]
         lib.oracle_hamming.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_uv_post.argtypes = [P, I, I, I, I, I, I, I, I, P]
+        lib.oracle_rectify.argtypes = [P, I, I, I, P, P, P]
         lib.oracle_sgm.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I] + [P] * 9
         for name in ("oracle_census", "oracle_cost_volume", "oracle_aggregate_path",
                      "oracle_sum_paths", "oracle_wta_left", "oracle_wta_right",
                      "oracle_lr_check", "oracle_median", "oracle_uvmap", "oracle_sgm",
-                     "oracle_hamming"):
+                     "oracle_hamming", "oracle_uv_post", "oracle_rectify"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -190,4 +192,27 @@ def sgm(left: np.ndarray, right: np.ndarray, D: int, census_w: int, census_h: in
         _p(g("DL")), _p(g("DR")), _p(g("lr")), _p(out["disp"]), _p(g("U")),
         _p(g("V")))
     _check(rc, "sgm")
+    return out
+
+
+def uv_post(m: np.ndarray, threshold: int, roi=None, dilate_r: int = 1) -> np.ndarray:
+    """Binary map of counts >= threshold inside roi = (r0, r1, c0, c1), dilated by a
+    (2r+1)^2 square, then 3x3 binomial Gaussian of 255 * binary (uint8)."""
+    m = np.ascontiguousarray(m, dtype=np.uint16)
+    rows, cols = m.shape
+    r0, r1, c0, c1 = roi if roi is not None else (0, rows, 0, cols)
+    out = np.empty((rows, cols), np.uint8)
+    _check(_load().oracle_uv_post(_p(m), rows, cols, threshold, r0, r1, c0, c1, dilate_r, _p(out)),
+           "uv_post")
+    return out
+
+
+def rectify(img: np.ndarray, mx: np.ndarray, my: np.ndarray) -> np.ndarray:
+    """I_rect(x, y) = I(mx(x, y), my(x, y)); 0 where the map leaves the image."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    mx = np.ascontiguousarray(mx, dtype=np.uint16)
+    my = np.ascontiguousarray(my, dtype=np.uint16)
+    out = np.empty((H, W), np.uint8)
+    _check(_load().oracle_rectify(_p(img), W, H, W, _p(mx), _p(my), _p(out)), "rectify")
     return out

@@ -10,12 +10,13 @@
  *
  * Paper: Ruf, Monka, Kollmann, Grinberg, "Real-time on-board obstacle
  * avoidance for UAVs based on embedded stereo vision" (ISPRS TC I, 2018).
+ *   Sec. 3.1.1 "Image rectification"      -> oracle_rectify
  *   Sec. 3.1.2 "Image matching", Eq. 1     -> oracle_census, oracle_cost_volume
  *   Sec. 3.1.3 "SGM optimization", Eq. 2   -> oracle_aggregate_path, oracle_sum_paths,
  *                                             oracle_wta_left
  *   Sec. 3.1.4 "Left-Right consistency"    -> oracle_wta_right, oracle_lr_check
  *   Sec. 3.1.5 "Median filter"             -> oracle_median
- *   Sec. 3.2   "Obstacle Avoidance"        -> oracle_uvmap
+ *   Sec. 3.2   "Obstacle Avoidance"        -> oracle_uvmap, oracle_uv_post
  *
  * Readings taken where the paper is silent or garbled (each is pinned by a
  * CPU test against brute force, a closed form or an invariant):
@@ -39,6 +40,15 @@
  *      is kept; k <= 1 copies the input.
  *   R8 U-map U[d][x] and V-map V[y][d] count pixels of the final map with
  *      value d < D; 0xFF is not counted.
+ *   R10 rectification maps point into a source image of the same W x H;
+ *      a rectified pixel whose map entry falls outside the source is 0.
+ *   R9 map post-processing (Sec. 3.2 names the steps, not their parameters):
+ *      binary B = (count >= threshold) inside the region of interest
+ *      [r0, r1) x [c0, c1) of the map, 0 outside it; dilation of B by a
+ *      (2r+1) x (2r+1) square (cells outside the map count as 0); then a
+ *      3x3 binomial Gaussian [1 2 1; 2 4 2; 1 2 1] / 16 of 255 * dilated
+ *      (cells outside the map count as 0), rounded half up:
+ *      out = (sum w * 255 * b + 8) / 16.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -348,4 +358,64 @@ done:
     free(DR);
     free(lr);
     return rc;
+}
+
+/* U-/V-map post-processing of Sec. 3.2, reading R9.  map is rows x cols
+ * uint16 (row-major); out is rows x cols uint8.  Threshold, region of
+ * interest, dilation, Gaussian, in that order. */
+int oracle_uv_post(const uint16_t *map, int rows, int cols, int threshold, int r0, int r1,
+                   int c0, int c1, int dilate_r, uint8_t *out)
+{
+    if (rows < 1 || cols < 1 || threshold < 0 || dilate_r < 0 || dilate_r > 7) return ORACLE_EINVAL;
+    size_t n = (size_t)rows * cols;
+    uint8_t *bin = (uint8_t *)malloc(n), *dil = (uint8_t *)malloc(n);
+    if (!bin || !dil) {
+        free(bin);
+        free(dil);
+        return ORACLE_ENOMEM;
+    }
+    for (int i = 0; i < rows; i++)
+        for (int j = 0; j < cols; j++) {
+            int inside = i >= r0 && i < r1 && j >= c0 && j < c1;
+            bin[(size_t)i * cols + j] = (uint8_t)(inside && map[(size_t)i * cols + j] >= threshold);
+        }
+    for (int i = 0; i < rows; i++)
+        for (int j = 0; j < cols; j++) {
+            int v = 0;
+            for (int u = -dilate_r; u <= dilate_r; u++)
+                for (int w = -dilate_r; w <= dilate_r; w++) {
+                    int ii = i + u, jj = j + w;
+                    if (ii >= 0 && ii < rows && jj >= 0 && jj < cols && bin[(size_t)ii * cols + jj]) v = 1;
+                }
+            dil[(size_t)i * cols + j] = (uint8_t)v;
+        }
+    static const int k[3] = {1, 2, 1};
+    for (int i = 0; i < rows; i++)
+        for (int j = 0; j < cols; j++) {
+            int acc = 0;
+            for (int u = -1; u <= 1; u++)
+                for (int w = -1; w <= 1; w++) {
+                    int ii = i + u, jj = j + w;
+                    if (ii >= 0 && ii < rows && jj >= 0 && jj < cols)
+                        acc += k[u + 1] * k[w + 1] * 255 * dil[(size_t)ii * cols + jj];
+                }
+            out[(size_t)i * cols + j] = (uint8_t)((acc + 8) / 16);
+        }
+    free(bin);
+    free(dil);
+    return ORACLE_OK;
+}
+
+/* Rectification, Sec. 3.1.1: I_rect(x, y) = I(M_x(x, y), M_y(x, y)) with
+ * integer maps of the rectified image's size (reading R10). */
+int oracle_rectify(const uint8_t *img, int W, int H, int pitch, const uint16_t *mx,
+                   const uint16_t *my, uint8_t *out)
+{
+    if (W < 1 || H < 1 || pitch < W) return ORACLE_EINVAL;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int sx = mx[(size_t)y * W + x], sy = my[(size_t)y * W + x];
+            out[(size_t)y * W + x] = (sx < W && sy < H) ? img[(size_t)sy * pitch + sx] : 0;
+        }
+    return ORACLE_OK;
 }

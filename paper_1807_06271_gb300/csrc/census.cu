@@ -22,20 +22,37 @@ constexpr int kRows = 4;  // rows per thread of the unrolled census kernel
 // the image": 255 is never darker than a centre pixel, which gives the 0 bit
 // the border rule asks for.  Each bit is the sign of I(q) - I(p), shifted
 // into one of two 32-bit halves (two instructions per bit).
-template <typename CodeT, int CW, int CH>
+// Pixel (gx, gy) of the rectified image: the source image read through the
+// maps (Sec. 3.1.1), 0 where a map entry leaves the source.
+template <bool RECT>
+__device__ __forceinline__ uint8_t rect_pixel(const uint8_t *__restrict__ img, int pitch, int W,
+                                              int H, int gx, int gy, const uint16_t *__restrict__ mx,
+                                              const uint16_t *__restrict__ my) {
+    if constexpr (!RECT) {
+        return img[(size_t)gy * pitch + gx];
+    } else {
+        const int sx = mx[(size_t)gy * W + gx], sy = my[(size_t)gy * W + gx];
+        return (sx < W && sy < H) ? img[(size_t)sy * pitch + sx] : 0;
+    }
+}
+
+template <typename CodeT, int CW, int CH, bool RECT>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
-                  int W, int H, CodeT *__restrict__ codes) {
+                  int W, int H, CodeT *__restrict__ codes, RectMaps maps) {
     constexpr int TW = kBX + CW - 1, TH = kBY * kRows + CH - 1;
     constexpr int RX = CW / 2, RY = CH / 2;
     __shared__ uint8_t tile[TH][TW];
     const uint8_t *img = blockIdx.z ? right : left;
+    const uint16_t *mx = blockIdx.z ? maps.rx : maps.lx, *my = blockIdx.z ? maps.ry : maps.ly;
     const int x0 = blockIdx.x * kBX - RX, y0 = blockIdx.y * kBY * kRows - RY;
     const int tid = threadIdx.y * kBX + threadIdx.x;
     for (int i = tid; i < TW * TH; i += kBX * kBY) {
         const int ty = i / TW, tx = i - ty * TW;
         const int gx = x0 + tx, gy = y0 + ty;
-        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * pitch + gx] : 255;
+        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H)
+                           ? rect_pixel<RECT>(img, pitch, W, H, gx, gy, mx, my)
+                           : 255;
     }
     __syncthreads();
     const int x = blockIdx.x * kBX + threadIdx.x;
@@ -70,20 +87,23 @@ __global__ void __launch_bounds__(kBX *kBY)
 }
 
 // Generic window (any odd size up to 64 bits), loops not unrolled.
-template <typename CodeT>
+template <typename CodeT, bool RECT>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel_any(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
-                      int W, int H, int cw, int ch, CodeT *__restrict__ codes) {
+                      int W, int H, int cw, int ch, CodeT *__restrict__ codes, RectMaps maps) {
     extern __shared__ uint16_t tile_any[];
     const int TW = kBX + cw - 1, TH = kBY + ch - 1;
     const int rx = cw / 2, ry = ch / 2;
     const uint8_t *img = blockIdx.z ? right : left;
+    const uint16_t *mx = blockIdx.z ? maps.rx : maps.lx, *my = blockIdx.z ? maps.ry : maps.ly;
     const int x0 = blockIdx.x * kBX - rx, y0 = blockIdx.y * kBY - ry;
     const int tid = threadIdx.y * kBX + threadIdx.x;
     for (int i = tid; i < TW * TH; i += kBX * kBY) {
         int ty = i / TW, tx = i - ty * TW;
         int gx = x0 + tx, gy = y0 + ty;
-        tile_any[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * pitch + gx] : 256;
+        tile_any[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H)
+                          ? (uint16_t)rect_pixel<RECT>(img, pitch, W, H, gx, gy, mx, my)
+                          : (uint16_t)256;
     }
     __syncthreads();
     const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
@@ -215,20 +235,31 @@ __global__ void __launch_bounds__(kCostThreads)
 }  // namespace
 
 cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
-                          int cw, int ch, int code_bytes, void *codes, cudaStream_t s) {
+                          int cw, int ch, int code_bytes, void *codes, const RectMaps &maps,
+                          cudaStream_t s) {
     dim3 block(kBX, kBY), grid((W + kBX - 1) / kBX, (H + kBY - 1) / kBY, 2);
     const dim3 grid4((W + kBX - 1) / kBX, (H + kBY * kRows - 1) / (kBY * kRows), 2);
+    const bool rect = maps.lx != nullptr;
+#define SGM_CENSUS(T, CWv, CHv)                                                                         \
+    do {                                                                                                \
+        if (rect) census_kernel<T, CWv, CHv, true><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (T *)codes, maps);  \
+        else census_kernel<T, CWv, CHv, false><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (T *)codes, maps);      \
+    } while (0)
     if (cw == 5 && ch == 5 && code_bytes == 4)
-        census_kernel<uint32_t, 5, 5><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (uint32_t *)codes);
+        SGM_CENSUS(uint32_t, 5, 5);
     else if (cw == 9 && ch == 7 && code_bytes == 8)
-        census_kernel<uint64_t, 9, 7><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (uint64_t *)codes);
+        SGM_CENSUS(uint64_t, 9, 7);
     else {
         size_t smem = (size_t)(kBX + cw - 1) * (kBY + ch - 1) * sizeof(uint16_t);
-        if (code_bytes == 4)
-            census_kernel_any<uint32_t><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint32_t *)codes);
-        else
-            census_kernel_any<uint64_t><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint64_t *)codes);
+        if (code_bytes == 4) {
+            if (rect) census_kernel_any<uint32_t, true><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint32_t *)codes, maps);
+            else census_kernel_any<uint32_t, false><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint32_t *)codes, maps);
+        } else {
+            if (rect) census_kernel_any<uint64_t, true><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint64_t *)codes, maps);
+            else census_kernel_any<uint64_t, false><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint64_t *)codes, maps);
+        }
     }
+#undef SGM_CENSUS
     return cudaGetLastError();
 }
 

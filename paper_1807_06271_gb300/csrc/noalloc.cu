@@ -85,7 +85,7 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     cudaStream_t s = (cudaStream_t)stream;
     const int pitch = params->row_pitch ? params->row_pitch : W;
     cudaError_t e = sgm::launch_census(left, right, pitch, W, H, params->census_w, params->census_h,
-                                       code_bytes, codes, s);
+                                       code_bytes, codes, sgm::RectMaps{nullptr, nullptr, nullptr, nullptr}, s);
     if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, s);
     if (e == cudaSuccess)
         e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, jobs, planes, npaths,

@@ -89,7 +89,7 @@ int run_census(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaS
     const int pitch = h->p.row_pitch ? h->p.row_pitch : h->W;
     TimingRecord *t = stage_begin(h, kStageCensus, s);
     cudaError_t e = launch_census(left, right, pitch, h->W, h->H, h->p.census_w, h->p.census_h,
-                                  h->code_bytes, h->codes, s);
+                                  h->code_bytes, h->codes, h->rect, s);
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
@@ -407,6 +407,16 @@ int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8
         cudaMemcpyAsync(disp_lr, h->disp_lr, (size_t)h->W * h->H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         rc = SGM_ERR_CUDA;
     return rc;
+}
+
+int sgm_set_rectification(sgm_handle h, const uint16_t *left_x, const uint16_t *left_y,
+                          const uint16_t *right_x, const uint16_t *right_y) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    const int set = (left_x != nullptr) + (left_y != nullptr) + (right_x != nullptr) + (right_y != nullptr);
+    if (set != 0 && set != 4) return SGM_ERR_INVALID_ARG;
+    h->rect = {left_x, left_y, right_x, right_y};
+    batch_forget(h);  // captured graphs hold the previous census launch
+    return SGM_OK;
 }
 
 int sgm_set_timing(sgm_handle h, int enable) {

@@ -28,6 +28,12 @@ inline long scanlines_of(int r, int W, int H) {
     return (long)W + H - 1;
 }
 
+// Rectification maps of the left and right image (device, W x H each; all
+// null when the images are already rectified).
+struct RectMaps {
+    const uint16_t *lx, *ly, *rx, *ry;
+};
+
 // Disparity layout.  The D disparities of a pixel are handled by LPS lanes
 // ("lanes per scanline", a power of two) with 8 disparities each, so a pixel
 // owns Dp = 8 * LPS bytes in the cost volume and in every path plane; slots
@@ -87,6 +93,7 @@ struct sgm_handle_s {
     uint8_t *disp_lr;   // [H][W] after the LR check, before the median
     unsigned *job_counter;  // work-queue head of the aggregation kernel
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
+    sgm::RectMaps rect;     // caller-owned rectification maps, or all null
 
     // device staging for sgm_compute_host, allocated on first use
     uint8_t *io_left, *io_right, *io_disp;
@@ -108,7 +115,8 @@ namespace sgm {
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
-                          int cw, int ch, int code_bytes, void *codes, cudaStream_t s);
+                          int cw, int ch, int code_bytes, void *codes, const RectMaps &maps,
+                          cudaStream_t s);
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
                         uint8_t *cost, cudaStream_t s);
 // Planes are pixel-interleaved: [H][W][nplanes][Dp], entry k of `jobs` writing

@@ -57,6 +57,11 @@ class SgmParams:
                        self.lr_tolerance, self.median_k, self.row_pitch)
 
 
+class _UvPost(ctypes.Structure):
+    _fields_ = [("u_threshold", ctypes.c_int), ("v_threshold", ctypes.c_int),
+                ("u_roi", ctypes.c_int * 4), ("v_roi", ctypes.c_int * 4), ("dilate_r", ctypes.c_int)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -77,6 +82,8 @@ _SIGNATURES = {
     "sgm_get_stage_times": [_P, _P, _P, _I, _P],
     "sgm_compute_static": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P, _P],
     "sgm_autotune": [_P, _P, _P, _P, _P, _P],
+    "uvmap_postprocess": [_P, _P, _P, ctypes.POINTER(_UvPost), _P, _P, _P],
+    "sgm_set_rectification": [_P, _P, _P, _P, _P],
 }
 
 SGM_STATIC_SCRATCH_BYTES = 32 << 20
@@ -326,3 +333,27 @@ def sgm_compute_static(W: int, H: int, D: int, params: SgmParams, left, right, d
         W, H, D, ctypes.byref(p), _dev(left, ("uint8",), shp, "left"),
         _dev(right, ("uint8",), shp, "right"), _dev(disp, ("uint8",), (H, W), "disp"),
         _stream(stream)), "sgm_compute_static")
+
+
+def uvmap_postprocess(h: Handle, umap, vmap, u_threshold: int, v_threshold: int, u_roi=None,
+                      v_roi=None, dilate_r: int = 1, uout=None, vout=None, stream=None):
+    """Thresholded, dilated and Gaussian-smoothed U-/V-maps (uint8) of Sec. 3.2."""
+    u_roi = u_roi or (0, h.D, 0, h.W)
+    v_roi = v_roi or (0, h.H, 0, h.D)
+    p = _UvPost(u_threshold, v_threshold, (ctypes.c_int * 4)(*u_roi), (ctypes.c_int * 4)(*v_roi),
+                dilate_r)
+    _check(load().uvmap_postprocess(
+        h.ptr, _dev(umap, ("uint16", "int16"), (h.D, h.W), "umap"),
+        _dev(vmap, ("uint16", "int16"), (h.H, h.D), "vmap"), ctypes.byref(p),
+        _dev(uout, ("uint8",), (h.D, h.W), "uout"), _dev(vout, ("uint8",), (h.H, h.D), "vout"),
+        _stream(stream)), "uvmap_postprocess")
+
+
+def sgm_set_rectification(h: Handle, left_x=None, left_y=None, right_x=None, right_y=None):
+    """Rectify the inputs of later calls through integer maps (device uint16/int16
+    tensors, H x W; keep them alive while h uses them); no arguments switch it off."""
+    shp = (h.H, h.W)
+    _check(load().sgm_set_rectification(
+        h.ptr, _dev(left_x, ("uint16", "int16"), shp, "left_x"), _dev(left_y, ("uint16", "int16"), shp, "left_y"), _dev(right_x, ("uint16", "int16"), shp, "right_x"),
+        _dev(right_y, ("uint16", "int16"), shp, "right_y")), "sgm_set_rectification")
+    h._rect = (left_x, left_y, right_x, right_y)  # keep the tensors alive

@@ -255,3 +255,73 @@ def test_stage_timing_counts_launches():
         assert t["census"][1] == 3 and t["aggregate"][1] == 3 and t["wta_lr"][1] == 3
         assert all(ms > 0 for ms, n in t.values() if n)
         assert sgm.sgm_get_stage_times(h)["aggregate"][1] == 0
+
+
+# ---------------------------------------------------------------------------
+# Next rows: map post-processing (Sec. 3.2) and rectification (Sec. 3.1.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("thr,rad,roi_frac", [(3, 1, None), (8, 2, (0.2, 0.9, 0.1, 0.8)), (1, 0, (0.5, 1.0, 0.0, 0.5))])
+def test_uv_postprocess_matches_oracle(thr, rad, roi_frac):
+    w = scenes.HD_1280
+    s = scenes.scene_for(w, scenes.workload_seed(2))
+    o = oracle.sgm(s.left, s.right, w.D, w.census_w, w.census_h, w.path_mask, w.P1, w.P2,
+                   w.lr_tol, w.median_k)
+    def roi(rows, cols):
+        if roi_frac is None:
+            return (0, rows, 0, cols)
+        a, b, c, d = roi_frac
+        return (int(a * rows), int(b * rows), int(c * cols), int(d * cols))
+    uroi, vroi = roi(w.D, w.W), roi(w.H, w.D)
+    with sgm.Handle(w.W, w.H, w.D, _workload_params(w)) as h:
+        disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
+        U = torch.empty((w.D, w.W), dtype=torch.int16, device="cuda")
+        V = torch.empty((w.H, w.D), dtype=torch.int16, device="cuda")
+        h.compute(cuda(s.left), cuda(s.right), disp)
+        h.uvmap(disp, U, V)
+        uo = torch.empty((w.D, w.W), dtype=torch.uint8, device="cuda")
+        vo = torch.empty((w.H, w.D), dtype=torch.uint8, device="cuda")
+        sgm.uvmap_postprocess(h, U, V, thr, 2 * thr, uroi, vroi, rad, uo, vo)
+        torch.cuda.synchronize()
+        assert_same(uo.cpu().numpy(), oracle.uv_post(o["U"], thr, uroi, rad), "U post")
+        assert_same(vo.cpu().numpy(), oracle.uv_post(o["V"], 2 * thr, vroi, rad), "V post")
+
+
+def _distorted_pair(W, H, D, seed):
+    """Left image as is; right image moved down 3 rows with a per-row shear,
+    and the integer maps that undo it."""
+    s = scenes.boxes_scene(W, H, D, seed=seed, n_boxes=3, dlo=2, dhi=D - 2)
+    y, x = np.mgrid[0:H, 0:W]
+    shear = (y // 8) % 3
+    raw = np.zeros_like(s.right)
+    ys, xs = y + 3, x + shear
+    ok = (ys < H) & (xs < W)
+    raw[ys[ok], xs[ok]] = s.right[ok]
+    maps = (x.astype(np.uint16), y.astype(np.uint16),
+            np.minimum(x + shear, 0xFFFF).astype(np.uint16), (y + 3).astype(np.uint16))
+    return s.left, raw, maps
+
+
+@pytest.mark.parametrize("W,H,D,cw,ch", [(96, 64, 32, 5, 5), (160, 90, 64, 9, 7), (77, 41, 16, 7, 9)])
+def test_rectified_pipeline_matches_oracle(W, H, D, cw, ch):
+    left, raw, (lx, ly, rx, ry) = _distorted_pair(W, H, D, seed=W + D)
+    p = params(cw, ch, 0xFF, 4, 24, 1, 3)
+    lr = oracle.rectify(left, lx, ly)
+    rr = oracle.rectify(raw, rx, ry)
+    o = oracle.sgm(lr, rr, D, cw, ch, 0xFF, 4, 24, 1, 3, stages=True)
+    with sgm.Handle(W, H, D, p) as h:
+        maps = [cuda(m.view(np.int16)) for m in (lx, ly, rx, ry)]
+        sgm.sgm_set_rectification(h, *maps)
+        cl = torch.empty((H, W), dtype=torch.int64, device="cuda")
+        cr = torch.empty_like(cl)
+        sgm.sgm_debug_census(h, cuda(left), cuda(raw), cl, cr)
+        disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        h.compute(cuda(left), cuda(raw), disp)
+        torch.cuda.synchronize()
+        assert_same(cl.cpu().numpy().view(np.uint64), o["codes_l"], "census left")
+        assert_same(cr.cpu().numpy().view(np.uint64), o["codes_r"], "census right")
+        assert_same(disp.cpu().numpy(), o["disp"], "disp")
+        sgm.sgm_set_rectification(h)  # off again: plain images
+        h.compute(cuda(lr), cuda(rr), disp)
+        torch.cuda.synchronize()
+        assert_same(disp.cpu().numpy(), o["disp"], "disp without maps")

@@ -333,3 +333,65 @@ def test_oracle_rejects_bad_arguments():
         oracle.aggregate_path(np.zeros((2, 2, 2), np.uint8), 0, 5, 2)  # P1 > P2
     with pytest.raises(ValueError):
         oracle.median(img, 4)
+
+
+# --------------------------------------------------------------------------
+# U-/V-map post-processing (Sec. 3.2): threshold, RoI, dilation, Gaussian
+# --------------------------------------------------------------------------
+
+def test_uv_post_single_cell_gives_dilated_binomial_footprint():
+    m = np.zeros((9, 11), np.uint16)
+    m[4, 5] = 7
+    out = oracle.uv_post(m, threshold=5, dilate_r=0)
+    k = np.outer([1, 2, 1], [1, 2, 1])
+    want = np.zeros((9, 11), np.int64)
+    want[3:6, 4:7] = (k * 255 + 8) // 16
+    assert np.array_equal(out, want)
+    # below threshold: nothing
+    assert not oracle.uv_post(m, threshold=8, dilate_r=1).any()
+
+
+def test_uv_post_matches_scipy_morphology_and_convolution():
+    ndi = pytest.importorskip("scipy.ndimage")
+    r = rng(80)
+    m = r.integers(0, 12, (40, 57)).astype(np.uint16)
+    for thr, rad, roi in [(9, 1, (5, 35, 3, 50)), (6, 2, (0, 40, 0, 57)), (11, 0, (10, 20, 10, 20))]:
+        b = np.zeros(m.shape, bool)
+        r0, r1, c0, c1 = roi
+        b[r0:r1, c0:c1] = m[r0:r1, c0:c1] >= thr
+        d = ndi.binary_dilation(b, structure=np.ones((2 * rad + 1,) * 2, bool)) if rad else b
+        g = ndi.convolve(d.astype(np.int64) * 255, np.outer([1, 2, 1], [1, 2, 1]), mode="constant")
+        assert np.array_equal(oracle.uv_post(m, thr, roi, rad), (g + 8) // 16)
+
+
+# --------------------------------------------------------------------------
+# Rectification (Sec. 3.1.1)
+# --------------------------------------------------------------------------
+
+def test_rectify_identity_shift_and_outside():
+    img = rng(90).integers(0, 256, (20, 30)).astype(np.uint8)
+    y, x = np.mgrid[0:20, 0:30]
+    assert np.array_equal(oracle.rectify(img, x, y), img)
+    # rows shifted by 3 and columns by 2: a plain numpy slice
+    out = oracle.rectify(img, np.minimum(x + 2, 29), np.minimum(y + 3, 19))
+    assert np.array_equal(out[:17, :28], img[3:, 2:])
+    # map entries outside the source image give 0
+    mx = x.copy()
+    mx[5, 7] = 30
+    out = oracle.rectify(img, mx, y)
+    assert out[5, 7] == 0 and np.array_equal(np.delete(out.ravel(), 5 * 30 + 7), np.delete(img.ravel(), 5 * 30 + 7))
+
+
+def test_rectify_undoes_a_known_distortion():
+    """A right image moved down 3 rows with a per-row horizontal shear is put
+    back exactly (away from the borders) by the inverse maps."""
+    s = scenes.boxes_scene(64, 48, 16, seed=91, n_boxes=2, dlo=2, dhi=12)
+    H, W = s.right.shape
+    y, x = np.mgrid[0:H, 0:W]
+    shear = (y // 8) % 3
+    raw = np.zeros_like(s.right)
+    ys, xs = y + 3, x + shear
+    ok = (ys < H) & (xs < W)
+    raw[ys[ok], xs[ok]] = s.right[ok]
+    back = oracle.rectify(raw, np.minimum(x + shear, 0xFFFF), y + 3)
+    assert np.array_equal(back[: H - 3, : W - 2], s.right[: H - 3, : W - 2])

@@ -4,35 +4,48 @@
 // Decomposition.  Every enabled direction cuts the image into independent
 // scanlines: rows for the horizontal directions, columns for the vertical
 // ones and W+H-1 diagonals for each diagonal direction.  The D disparities of
-// one pixel are held by LPS lanes, 8 disparities per lane, so one warp walks
-// G = 32 / LPS neighbouring scanlines in lock-step (D = 128: two scanlines).
-// The kernel is persistent: warps pull jobs (one direction, G scanlines)
-// from a global counter, the longest scanlines first, until the list is
-// exhausted; blocks_per_sm blocks of 4 warps run on every SM.  Two blocks
-// (two warps per scheduler) measured fastest: the horizontal scanlines, the
-// longest, set the kernel's duration, and each extra co-resident warp takes
-// issue slots from them.
+// one pixel are held by LPS lanes, DPL = 8 disparities per lane, so one warp
+// walks G = 32 / LPS neighbouring scanlines in lock-step (D = 128: two
+// scanlines of 16 lanes).  The kernel is persistent: blocks_per_sm blocks of
+// 4 warps run on every SM and pull jobs (one direction, G scanlines) from a
+// work queue until it is empty.  The long-axis scanlines (rows when W >= H)
+// set the kernel's duration, and they run about 1.5x slower when two of them
+// share a warp scheduler, so each scheduler takes at most one of them first
+// (see next_job); the other warps fill the issue slots left with the
+// remaining directions.  Three blocks per SM measured fastest on the
+// 1242 x 375, D = 128 workload; sgm_autotune picks the count per shape.
 //
-// Arithmetic.  A lane keeps its 8 path costs as four packed 16-bit pairs
-// R_k = (L[k], L[k+4]), k = 0..3.  With this interleaving the d-1 / d+1
-// neighbours of R1 and R2 are the registers R0/R2 and R1/R3 themselves, and
-// those of R0 and R3 cost one byte-permute each with the value fetched from
-// the neighbouring lane (one shuffle each way).  One update is
+// Arithmetic.  A lane keeps its DPL path costs as DPL/2 packed 16-bit pairs
+// R_k = (L[k], L[k+h]), h = DPL/2.  With this interleaving the d-1 / d+1
+// neighbours of the inner registers are the registers R_{k-1} / R_{k+1}
+// themselves, and those of the first and last cost one byte-permute each
+// with the value fetched from the neighbouring lane (one shuffle each way).
+// One update is
 //     t = min(min(L(d-1), L(d+1)) + P1, L(d), m + P2);   L' = t + C - m
 // evaluated two disparities at a time with the full-rate min.u16x2 and plain
 // 32-bit adds (no half ever carries: values stay below 0x7FFF + 255, and
 // t >= m makes t + C - m non-negative in each half).  m = min_d L is reduced
-// within the lane (3 min.u16x2), then across the scanline's lanes with
-// one full-warp redux.sync per scanline of the warp.
-// Starting from L = 0, m = 0 makes the first step produce L = C without a
-// special case.  Disparities d >= D (padding) are parked at 0x7FFF so they
-// never win a minimum or act as a neighbour.
+// within the lane (min.u16x2), then across the scanline's lanes: xor-shuffles
+// for scanlines of up to 4 lanes, one full-warp redux.sync per scanline of
+// the warp for wider ones (an xor-shuffle tree over 16 lanes measured 1.5x
+// slower).  Starting from L = 0, m = 0 makes the first step produce L = C
+// without a special case.  Disparities d >= D (padding) are parked at 0x7FFF
+// so they never win a minimum or act as a neighbour.
+//
+// Measured and rejected on GB300: 16 disparities per lane (15 % fewer
+// instructions, but the fatter long-axis warps lengthen the critical path);
+// taking the next minimum from the previous step's costs, which moves the
+// reduction off the step-to-step chain (15 % more instructions, slower); a
+// 24-step cost ring.
 //
 // Memory.  The cost of step t + PF is loaded while step t computes (a ring of
-// PF = 16 8-byte registers), with an L2 evict_last hint: all directions
-// re-read the volume; the line of step t + 32 is prefetched into L2 at step t.  Each step stores the lane's 8 path costs (8 bytes) to the
-// direction's plane, in the cost volume's byte order, with evict_first: the
-// planes are read back only once, by the WTA kernel.
+// PF = 16 DPL-byte registers), with an L2 evict_last hint: all directions
+// re-read the volume; the line of step t + 32 is prefetched into L2 at step t.
+// While every scanline of the warp has more than 48 steps left the loop runs
+// without bounds checks.  Each
+// step stores the lane's DPL path costs to the direction's plane, in the cost
+// volume's byte order, with evict_first: the planes are read back only once,
+// by the WTA kernel.
 #include "sgm_internal.cuh"
 
 namespace sgm {
@@ -52,6 +65,7 @@ PathJobs make_path_jobs(int W, int H, int D, int mask) {
         j.plane[k] = __builtin_popcount((unsigned)mask & ((1u << r) - 1u));
         j.nlines[k] = (int)scanlines_of(r, W, H);
         j.jbegin[k + 1] = j.jbegin[k] + (j.nlines[k] + G - 1) / G;
+        if (i < 2) j.nlong = j.jbegin[k + 1];
     }
     return j;
 }
@@ -60,7 +74,6 @@ namespace {
 
 constexpr int kWarps = 4;
 constexpr int kL2Ahead = 32;  // steps between the L2 prefetch of a cost line and its use
-constexpr uint32_t kInf2 = 0x7FFF7FFFu;
 constexpr uint32_t kLo = 0x00FF00FFu;
 
 __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
@@ -87,117 +100,211 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
-__device__ __forceinline__ uint2 ld_cost(const uint2 *p, uint64_t pol) {
-    uint2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-                 : "=r"(v.x), "=r"(v.y)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ void prefetch_l2(const uint2 *p) {
+__device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
 }
-__device__ __forceinline__ void st_plane(uint2 *p, uint2 v, uint64_t pol) {
-    asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x),
-                 "r"(v.y), "l"(pol)
-                 : "memory");
+
+// Job scheduling.  The long-axis scanlines (rows when W >= H) set the
+// kernel's duration: one of them takes about 145 cycles per step on a warp
+// scheduler of its own and much longer when two share a scheduler.  So the
+// first warp on each (SM, scheduler) slot that claims the slot takes a
+// long-axis job, the other warps start on the remaining directions, and after
+// its first job every warp drains the long-axis jobs first.  The slot comes
+// from %smid and %warpid (warp slot modulo the 4 schedulers): the placement
+// only affects speed, never results.
+__device__ __forceinline__ unsigned sched_slot() {
+    unsigned w, sm;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(w));
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    return sm * 4u + (w & 3u);
+}
+
+__device__ __forceinline__ unsigned next_job(unsigned *state, unsigned nlong, unsigned total, bool first) {
+    bool want_long = true;
+    if (first) {
+        const unsigned slot = sched_slot();
+        want_long = slot < (unsigned)kJobClaimSlots && atomicExch(state + kJobClaimBase + slot, 1u) == 0u;
+    }
+    if (want_long) {
+        const unsigned j = atomicAdd(state, 1u);
+        if (j < nlong) return j;
+        return nlong + atomicAdd(state + 1, 1u);
+    }
+    const unsigned j = nlong + atomicAdd(state + 1, 1u);
+    if (j < total) return j;
+    const unsigned jl = atomicAdd(state, 1u);
+    return jl < nlong ? jl : total;
+}
+
+// Chunk of DPL bytes: 8 -> uint2, 16 -> uint4.
+template <int DPL>
+struct Chunk;
+template <>
+struct Chunk<8> {
+    using T = uint2;
+    static __device__ __forceinline__ T zero() { return make_uint2(0u, 0u); }
+    static __device__ __forceinline__ uint32_t word(const T &c, int w) { return w == 0 ? c.x : c.y; }
+};
+template <>
+struct Chunk<16> {
+    using T = uint4;
+    static __device__ __forceinline__ T zero() { return make_uint4(0u, 0u, 0u, 0u); }
+    static __device__ __forceinline__ uint32_t word(const T &c, int w) {
+        return w == 0 ? c.x : w == 1 ? c.y : w == 2 ? c.z : c.w;
+    }
+};
+
+template <int DPL>
+__device__ __forceinline__ typename Chunk<DPL>::T ld_chunk(const typename Chunk<DPL>::T *p, uint64_t pol) {
+    typename Chunk<DPL>::T v;
+    if constexpr (DPL == 8) {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                     : "=r"(v.x), "=r"(v.y)
+                     : "l"(p), "l"(pol));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(p), "l"(pol));
+    }
+    return v;
+}
+template <int DPL>
+__device__ __forceinline__ void st_chunk(typename Chunk<DPL>::T *p, const typename Chunk<DPL>::T &v,
+                                         uint64_t pol) {
+    if constexpr (DPL == 8) {
+        asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p),
+                     "r"(v.x), "r"(v.y), "l"(pol)
+                     : "memory");
+    } else {
+        asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+                     "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+                     : "memory");
+    }
 }
 
 // (m, m) with m the minimum over the LPS lanes of this lane's scanline of
-// both halves of x.  One full-warp redux.sync per scanline of the warp, each
-// fed 0xFFFF by the lanes of the other scanlines (redux.sync with per-group
-// masks measured 2.4x slower on GB300).
+// both halves of x.  The halves are folded first ((m, m) = m * 0x10001 is
+// monotonic in m, so it can be reduced as one 32-bit value).  Scanlines of up
+// to 4 lanes reduce with xor-shuffles; wider ones use one full-warp
+// redux.sync per scanline of the warp, fed 0xFFFFFFFF by the other
+// scanlines' lanes (redux.sync with per-scanline masks measured 2.4x slower
+// on GB300).
 template <int LPS>
 __device__ __forceinline__ uint32_t line_min2(uint32_t x, int grp) {
     constexpr int G = 32 / LPS;
-    const uint32_t m32 = min(x & 0xFFFFu, x >> 16);
-    uint32_t m;
-    if constexpr (LPS == 1) {
-        m = m32;
+    x = vmin2(x, __byte_perm(x, 0u, 0x1032));
+    if constexpr (LPS <= 4) {
+#pragma unroll
+        for (int o = 1; o < LPS; o <<= 1) x = vmin2(x, __shfl_xor_sync(0xffffffffu, x, o));
+        return x;
     } else if constexpr (G == 1) {
-        m = __reduce_min_sync(0xffffffffu, m32);
+        return __reduce_min_sync(0xffffffffu, x);
+    } else if constexpr (G == 2) {
+        const uint32_t r0 = __reduce_min_sync(0xffffffffu, grp == 0 ? x : 0xFFFFFFFFu);
+        const uint32_t r1 = __reduce_min_sync(0xffffffffu, grp == 1 ? x : 0xFFFFFFFFu);
+        return grp ? r1 : r0;
     } else {
-        m = 0;
+        uint32_t m = 0;
 #pragma unroll
         for (int g = 0; g < G; g++) {
-            const uint32_t r = __reduce_min_sync(0xffffffffu, grp == g ? m32 : 0xFFFFu);
+            const uint32_t r = __reduce_min_sync(0xffffffffu, grp == g ? x : 0xFFFFFFFFu);
             if (grp == g) m = r;
         }
+        return m;
     }
-    return m * 0x00010001u;
 }
 
-// Path state of one lane: R_k = (L[k], L[k+4]) packed, m2 = (m, m), mP2 = m2 + (P2, P2).
+// Path state of one lane: R[k] = (L[k], L[k+h]) packed (h = DPL/2),
+// m2 = (m, m), mP2 = m2 + (P2, P2).
+template <int DPL>
 struct PathState {
-    uint32_t R0, R1, R2, R3, m2, mP2;
+    uint32_t R[DPL / 2];
+    uint32_t m2, mP2;
 };
 
-// One step of Eq. 2 for the lane's 8 disparities with cost chunk c.
-template <int LPS, bool RAGGED>
-__device__ __forceinline__ void path_step(PathState &st, uint2 c, uint32_t P1x2, uint32_t P2x2,
-                                          int grp, uint32_t lo_edge, uint32_t hi_edge,
-                                          const uint32_t (&inv)[4]) {
-    // bytes (1, 3) of a word, zero-extended to 16-bit halves, in one byte-permute
-    const uint32_t c0 = c.x & kLo, c1 = __byte_perm(c.x, 0u, 0x4341);
-    const uint32_t c2 = c.y & kLo, c3 = __byte_perm(c.y, 0u, 0x4341);
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, st.R3, 1);
-    const uint32_t next = __shfl_down_sync(0xffffffffu, st.R0, 1);
-    // (L[-1], L[3]) and (L[4], L[8]); the first/last lane of a scanline ORs in
-    // 0x7FFF for the missing neighbour (lo_edge / hi_edge are 0 elsewhere)
-    const uint32_t dm0 = __byte_perm(prev, st.R3, 0x5432) | lo_edge;
-    const uint32_t dp3 = __byte_perm(st.R0, next, 0x5432) | hi_edge;
-    uint32_t n0 = vmin2(vmin2(vmin2(dm0, st.R1) + P1x2, st.R0), st.mP2) + c0 - st.m2;
-    uint32_t n1 = vmin2(vmin2(vmin2(st.R0, st.R2) + P1x2, st.R1), st.mP2) + c1 - st.m2;
-    uint32_t n2 = vmin2(vmin2(vmin2(st.R1, st.R3) + P1x2, st.R2), st.mP2) + c2 - st.m2;
-    uint32_t n3 = vmin2(vmin2(vmin2(st.R2, dp3) + P1x2, st.R3), st.mP2) + c3 - st.m2;
-    if (RAGGED) {
-        n0 = vmax2(n0, inv[0]);
-        n1 = vmax2(n1, inv[1]);
-        n2 = vmax2(n2, inv[2]);
-        n3 = vmax2(n3, inv[3]);
+// One step of Eq. 2 for the lane's DPL disparities with cost chunk c.
+template <int LPS, int DPL, bool RAGGED>
+__device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Chunk<DPL>::T &c,
+                                          uint32_t P1x2, uint32_t P2x2, int grp, uint32_t lo_edge,
+                                          uint32_t hi_edge, const uint32_t (&inv)[DPL / 2]) {
+    constexpr int NR = DPL / 2;
+    uint32_t cc[NR];
+#pragma unroll
+    for (int w = 0; w < DPL / 4; w++) {
+        const uint32_t v = Chunk<DPL>::word(c, w);
+        cc[2 * w] = v & kLo;                         // bytes 0, 2
+        cc[2 * w + 1] = __byte_perm(v, 0u, 0x4341);  // bytes 1, 3
     }
-    st.R0 = n0;
-    st.R1 = n1;
-    st.R2 = n2;
-    st.R3 = n3;
-    st.m2 = line_min2<LPS>(vmin2(vmin2(n0, n1), vmin2(n2, n3)), grp);
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, st.R[NR - 1], 1);
+    const uint32_t next = __shfl_down_sync(0xffffffffu, st.R[0], 1);
+    // (L[-1], L[h-1]) and (L[h], L[DPL]); the first/last lane of a scanline ORs
+    // in 0x7FFF for the missing neighbour (lo_edge / hi_edge are 0 elsewhere)
+    const uint32_t dm0 = __byte_perm(prev, st.R[NR - 1], 0x5432) | lo_edge;
+    const uint32_t dpN = __byte_perm(st.R[0], next, 0x5432) | hi_edge;
+    uint32_t n[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) {
+        const uint32_t lm = k == 0 ? dm0 : st.R[k - 1];
+        const uint32_t rm = k == NR - 1 ? dpN : st.R[k + 1];
+        n[k] = vmin2(vmin2(vmin2(lm, rm) + P1x2, st.R[k]), st.mP2) + cc[k] - st.m2;
+        if (RAGGED) n[k] = vmax2(n[k], inv[k]);
+    }
+    uint32_t mn = n[0];
+#pragma unroll
+    for (int k = 0; k < NR; k++) {
+        st.R[k] = n[k];
+        if (k) mn = vmin2(mn, n[k]);
+    }
+    st.m2 = line_min2<LPS>(mn, grp);
     st.mP2 = st.m2 + P2x2;
 }
 
-// The lane's 8 path costs as the plane's 8 bytes (cost-volume byte order).
-template <bool RAGGED>
-__device__ __forceinline__ uint2 pack_plane(const PathState &st) {
-    uint32_t o0 = st.R0, o1 = st.R1, o2 = st.R2, o3 = st.R3;
-    if (RAGGED) {
-        o0 &= kLo;
-        o1 &= kLo;
-        o2 &= kLo;
-        o3 &= kLo;
+// The lane's DPL path costs as the plane's bytes (cost-volume byte order).
+template <int DPL, bool RAGGED>
+__device__ __forceinline__ typename Chunk<DPL>::T pack_plane(const PathState<DPL> &st) {
+    uint32_t w[DPL / 4];
+#pragma unroll
+    for (int i = 0; i < DPL / 4; i++) {
+        uint32_t a = st.R[2 * i], b = st.R[2 * i + 1];
+        if (RAGGED) {
+            a &= kLo;
+            b &= kLo;
+        }
+        w[i] = b * 256u + a;
     }
-    return make_uint2(o1 * 256u + o0, o3 * 256u + o2);
+    if constexpr (DPL == 8) return make_uint2(w[0], w[1]);
+    else return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-template <int LPS, bool RAGGED, int PF>
+template <int LPS, int DPL, bool RAGGED, int PF>
 __global__ void __launch_bounds__(kWarps * 32)
-    aggregate_kernel(const uint2 *__restrict__ cost, int W, int H, int D, uint32_t P1x2,
-                     uint32_t P2x2, PathJobs jobs, uint2 *__restrict__ planes, int nplanes,
+    aggregate_kernel(const typename Chunk<DPL>::T *__restrict__ cost, int W, int H, int D,
+                     uint32_t P1x2, uint32_t P2x2, PathJobs jobs,
+                     typename Chunk<DPL>::T *__restrict__ planes, int nplanes,
                      unsigned *__restrict__ job_counter) {
-    constexpr int G = 32 / LPS;
+    using CT = typename Chunk<DPL>::T;
+    constexpr int G = 32 / LPS, NR = DPL / 2;
+    static_assert(kL2Ahead >= PF, "the unchecked loop assumes the prefetch runs ahead of the ring");
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPS, li = lane % LPS;
-    const uint32_t lo_edge = li == 0 ? 0x7FFFu : 0u;              // no d = -1
-    const uint32_t hi_edge = li == LPS - 1 ? 0x7FFF0000u : 0u;    // no d = Dp
+    const uint32_t lo_edge = li == 0 ? 0x7FFFu : 0u;            // no d = -1
+    const uint32_t hi_edge = li == LPS - 1 ? 0x7FFF0000u : 0u;  // no d = Dp
     const int total = jobs.jbegin[jobs.n];
     const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
-    uint32_t inv[4] = {0u, 0u, 0u, 0u};
-    if (RAGGED) {
+    uint32_t inv[NR];
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            inv[k] = (8 * li + k >= D ? 0x7FFFu : 0u) | (8 * li + k + 4 >= D ? 0x7FFF0000u : 0u);
+    for (int k = 0; k < NR; k++) {
+        inv[k] = 0u;
+        if (RAGGED)
+            inv[k] = (DPL * li + k >= D ? 0x7FFFu : 0u) | (DPL * li + k + NR >= D ? 0x7FFF0000u : 0u);
     }
+    // one lane per 128-byte line of a pixel's cost record prefetches into L2
+    const bool pf_lane = ((DPL * li) & 127) == 0;
+    bool first = true;
     for (;;) {
         unsigned job = 0;
-        if (lane == 0) job = atomicAdd(job_counter, 1u);
+        if (lane == 0) job = next_job(job_counter, (unsigned)jobs.nlong, (unsigned)total, first);
+        first = false;
         job = __shfl_sync(0xffffffffu, job, 0);
         if (job >= (unsigned)total) return;
         int k = 0;
@@ -226,39 +333,58 @@ __global__ void __launch_bounds__(kWarps * 32)
             }
         }
         const int steps = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
-        // 8-byte-unit indices: cost chunk (x, y, li) is cost[(y*W + x)*LPS + li], plane
-        // chunk is planes[((y*W + x)*nplanes + plane)*LPS + li] (all planes of a pixel
-        // are adjacent).  Indices stay below 2^31 (checked when the handle is made).
+        // chunk indices: cost chunk (x, y, li) is cost[(y*W + x)*LPS + li], plane
+        // chunk is planes[((y*W + x)*nplanes + plane)*LPS + li] (all planes of a
+        // pixel are adjacent).  Indices stay below 2^31 (checked at handle creation).
         const int pix = y * W + x;
         const int cstep = (dy * W + dx) * LPS;
         const int ostep = cstep * nplanes;
         int ci_ld = pix * LPS + li;  // next cost chunk to load into the ring
-        // one lane per 128-byte line of a pixel's cost record prefetches into L2
-        const bool pf_lane = ((8 * li) & 127) == 0;
         int ci_pf = ci_ld;
         if (pf_lane)
             for (int i = 0; i < kL2Ahead && i < len; i++) prefetch_l2(cost + ci_pf + i * cstep);
         ci_pf += kL2Ahead * cstep;
         int oi = (pix * nplanes + jobs.plane[k]) * LPS + li;
-        uint2 ring[PF];
+        CT ring[PF];
 #pragma unroll
         for (int i = 0; i < PF; i++) {
-            ring[i] = i < len ? ld_cost(cost + ci_ld, pol_keep) : make_uint2(0u, 0u);
+            ring[i] = i < len ? ld_chunk<DPL>(cost + ci_ld, pol_keep) : Chunk<DPL>::zero();
             ci_ld += cstep;
         }
-        PathState st = {inv[0], inv[1], inv[2], inv[3], 0u, P2x2};
+        PathState<DPL> st;
+#pragma unroll
+        for (int q = 0; q < NR; q++) st.R[q] = inv[q];
+        st.m2 = 0u;
+        st.mP2 = P2x2;
         int rem = len;  // steps of this lane's scanline not yet taken
         int t0 = 0;
+        // While every scanline of the warp has more than kL2Ahead + PF steps
+        // left, the loads, prefetches and stores need no checks.
+        const int minlen = (int)__reduce_min_sync(0xffffffffu, (unsigned)len);
+        for (; t0 + PF + kL2Ahead <= minlen; t0 += PF) {
+#pragma unroll
+            for (int i = 0; i < PF; i++) {
+                const CT c = ring[i];
+                ring[i] = ld_chunk<DPL>(cost + ci_ld, pol_keep);
+                ci_ld += cstep;
+                if (pf_lane) prefetch_l2(cost + ci_pf);
+                ci_pf += cstep;
+                path_step<LPS, DPL, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+                st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
+                oi += ostep;
+            }
+            rem -= PF;
+        }
         for (; t0 + PF <= steps; t0 += PF) {
 #pragma unroll
             for (int i = 0; i < PF; i++) {
-                const uint2 c = ring[i];
-                if (rem > PF) ring[i] = ld_cost(cost + ci_ld, pol_keep);
+                const CT c = ring[i];
+                if (rem > PF) ring[i] = ld_chunk<DPL>(cost + ci_ld, pol_keep);
                 ci_ld += cstep;
                 if (pf_lane && rem > kL2Ahead) prefetch_l2(cost + ci_pf);
                 ci_pf += cstep;
-                path_step<LPS, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                if (rem > 0) st_plane(planes + oi, pack_plane<RAGGED>(st), pol_stream);
+                path_step<LPS, DPL, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+                if (rem > 0) st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
                 oi += ostep;
                 rem--;
             }
@@ -266,8 +392,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
         for (int i = 0; i < PF; i++) {  // the last steps < PF
             if (t0 + i < steps) {
-                path_step<LPS, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                if (rem > 0) st_plane(planes + oi, pack_plane<RAGGED>(st), pol_stream);
+                path_step<LPS, DPL, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+                if (rem > 0) st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
                 oi += ostep;
                 rem--;
             }
@@ -275,28 +401,29 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 }
 
-template <int LPS>
+template <int LPS, int DPL>
 cudaError_t launch_lps(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                        const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
                        int blocks, cudaStream_t s) {
-    constexpr int PF = 16;  // cost loads issued 16 steps ahead
-    const uint2 *c = reinterpret_cast<const uint2 *>(cost);
-    uint2 *p = reinterpret_cast<uint2 *>(planes);
-    if (D == 8 * LPS)
-        aggregate_kernel<LPS, false, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
+    using CT = typename Chunk<DPL>::T;
+    constexpr int PF = 16;  // cost loads issued PF steps ahead
+    const CT *c = reinterpret_cast<const CT *>(cost);
+    CT *p = reinterpret_cast<CT *>(planes);
+    if (D == DPL * LPS)
+        aggregate_kernel<LPS, DPL, false, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
     else
-        aggregate_kernel<LPS, true, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
+        aggregate_kernel<LPS, DPL, true, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
     return cudaGetLastError();
 }
 
 // Plane 0 ([H][W][Dp], lane-chunk byte order) -> L ([H][W][D], natural order).
-__global__ void unpermute_kernel(const uint8_t *__restrict__ plane, int npx, int D, int Dp,
+__global__ void unpermute_kernel(const uint8_t *__restrict__ plane, int npx, int D, int Dp, int dpl,
                                  uint8_t *__restrict__ L) {
     const size_t n = (size_t)npx * D;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t p = i / D;
         const int d = (int)(i - p * D);
-        L[i] = plane[p * Dp + 8 * (d >> 3) + chunk_byte_of(d & 7)];
+        L[i] = plane[p * Dp + dpl * (d / dpl) + chunk_byte(dpl, d % dpl)];
     }
 }
 
@@ -306,7 +433,7 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
                              unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
     if (jobs.jbegin[jobs.n] == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(job_counter, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(job_counter, 0, kJobStateBytes, s);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
@@ -314,14 +441,16 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
     if (e != cudaSuccess) return e;
     const int blocks = sms * (blocks_per_sm > 0 ? blocks_per_sm : 2);
     const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
+#define SGM_AGG(L, P) launch_lps<L, P>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s)
     switch (lanes_per_scanline(D)) {
-        case 1: return launch_lps<1>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
-        case 2: return launch_lps<2>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
-        case 4: return launch_lps<4>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
-        case 8: return launch_lps<8>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
-        case 16: return launch_lps<16>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
-        default: return launch_lps<32>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+        case 1: return SGM_AGG(1, 8);
+        case 2: return SGM_AGG(2, 8);
+        case 4: return SGM_AGG(4, 8);
+        case 8: return SGM_AGG(8, 8);
+        case 16: return SGM_AGG(16, 8);
+        default: return SGM_AGG(32, 8);
     }
+#undef SGM_AGG
 }
 
 cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, uint8_t *L, cudaStream_t s) {
@@ -329,7 +458,7 @@ cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, uint8_t 
     const size_t n = (size_t)npx * D;
     const size_t want = (n + 255) / 256;
     const int blocks = (int)(want < 4096 ? want : 4096);
-    unpermute_kernel<<<blocks, 256, 0, s>>>(plane, npx, D, padded_disparities(D), L);
+    unpermute_kernel<<<blocks, 256, 0, s>>>(plane, npx, D, padded_disparities(D), disparities_per_lane(D), L);
     return cudaGetLastError();
 }
 

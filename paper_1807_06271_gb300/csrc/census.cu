@@ -9,6 +9,8 @@
 // skipped) is darker than the centre.  Codes of up to 32 bits are stored as
 // uint32, longer ones as uint64.  HBM traffic: 1 byte read + 4/8 bytes
 // written per pixel and image.
+#include <type_traits>
+
 #include "sgm_internal.cuh"
 
 namespace sgm {
@@ -125,13 +127,14 @@ __global__ void __launch_bounds__(kBX *kBY)
 // or the code width when x-d < 0, for d < D; padding slots d >= D hold the
 // code width too.  One CTA per segment of kSeg pixels of one row: the
 // segment's left codes and the right codes it reaches (kSeg + Dp + 2 of them)
-// are staged in shared memory.  A thread computes one 8-disparity chunk of two
-// neighbouring pixels from 9 consecutive right codes read as aligned vectors,
-// with consecutive threads on consecutive pixel pairs (conflict-free reads); the segment is transposed
-// through a padded shared tile and written out with coalesced 8-byte stores
-// (the segment's Dp-byte pixel records are contiguous in global memory).
-// popc runs on the XU pipe (16 per SM per clock; two per estimate for 64-bit
-// codes), which bounds this kernel.
+// are staged in shared memory.  A thread computes one DPL-disparity chunk of
+// two neighbouring pixels from DPL + 1 consecutive right codes read as
+// aligned vectors, with consecutive threads on consecutive pixel pairs
+// (conflict-free reads); the segment is transposed through a padded shared
+// tile and written out with coalesced DPL-byte stores (the segment's Dp-byte
+// pixel records are contiguous in global memory).  popc runs on the XU pipe
+// (16 per SM per clock; two per estimate for 64-bit codes), which bounds
+// this kernel.
 // ---------------------------------------------------------------------------
 
 constexpr int kCostThreads = 256, kSeg = 64;
@@ -139,12 +142,29 @@ constexpr int kCostThreads = 256, kSeg = 64;
 __device__ __forceinline__ uint32_t popcnt(uint32_t v) { return __popc(v); }
 __device__ __forceinline__ uint32_t popcnt(uint64_t v) { return __popcll(v); }
 
-template <typename CodeT, bool RAGGED>
+// Bytes of one chunk word: word w of a lane holds disparities 2w, 2w+1, 2w+h, 2w+1+h
+// (h = DPL/2) in its bytes 0..3, the order in which the aggregation unpacks them.
+template <int DPL>
+__device__ __forceinline__ void pack_chunk(const uint32_t (&c)[DPL], uint32_t (&w)[DPL / 4]) {
+    constexpr int h = DPL / 2;
+#pragma unroll
+    for (int i = 0; i < DPL / 4; i++)
+        w[i] = (c[2 * i + 1 + h] * 256u + c[2 * i + h]) * 65536u + (c[2 * i + 1] * 256u + c[2 * i]);
+}
+
+template <int DPL>
+__device__ __forceinline__ void st_shared_chunk(uint8_t *p, const uint32_t (&w)[DPL / 4]) {
+    if constexpr (DPL == 8) *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    else *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <typename CodeT, int DPL, bool RAGGED>
 __global__ void __launch_bounds__(kCostThreads)
     cost_kernel(const CodeT *__restrict__ codes, int W, int H, int D, int Dp, int nbits,
                 uint8_t *__restrict__ cost) {
+    using VecT = typename std::conditional<DPL == 8, uint2, uint4>::type;
     extern __shared__ __align__(16) unsigned char cost_smem[];
-    const int stride = Dp + 8;  // padded tile row (bytes)
+    const int stride = Dp + DPL;  // padded tile row (bytes)
     uint8_t *tile = cost_smem;                                          // [kSeg][stride]
     const int tile_bytes = (kSeg * stride + 15) & ~15;
     CodeT *cl = reinterpret_cast<CodeT *>(cost_smem + tile_bytes);     // [kSeg]
@@ -159,35 +179,32 @@ __global__ void __launch_bounds__(kCostThreads)
         cr[i] = (xr >= 0 && xr < W) ? rowr[xr] : 0;
     }
     __syncthreads();
-    const int chunks = Dp / 8;
+    const int chunks = Dp / DPL;
     const bool border = x0 < Dp;  // only the first segments see x - d < 0
-    // A thread takes one 8-disparity chunk of the pixel pair (px, px+1), px even.
+    // A thread takes one DPL-disparity chunk i of the pixel pair (px, px+1), px even.
     // Column x - d of pixel px sits at cr[px - d + Dp + 1]: for the chunk's
-    // disparities 8i+j the pair needs the 9 codes w[k] = cr[s + k], s = px + Dp - 8i - 6
-    // (even, so the run is 16-byte aligned for 8-byte codes): pixel px uses
-    // w[7 - j], pixel px + 1 uses w[8 - j].
+    // disparities DPL*i + j the pair needs the DPL + 1 codes w[k] = cr[s + k],
+    // s = px + Dp + 2 - DPL*(i + 1) (even, so the run is 16-byte aligned for
+    // 8-byte codes; 2 <= s and s + DPL <= kSeg + Dp): pixel px uses
+    // w[DPL - 1 - j], pixel px + 1 uses w[DPL - j].
     for (int it = threadIdx.x; it < (kSeg / 2) * chunks; it += kCostThreads) {
         const int pr = it % (kSeg / 2), i = it / (kSeg / 2);
         const int px = 2 * pr;
-        const int sidx = px + Dp - 8 * i - 6;
-        CodeT w[9];
-        if constexpr (sizeof(CodeT) == 8) {
+        const int sidx = px + Dp + 2 - DPL * (i + 1);
+        CodeT w[DPL + 1];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < DPL / 2; k++) {
+            if constexpr (sizeof(CodeT) == 8) {
                 const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cr + sidx + 2 * k);
                 w[2 * k] = v.x;
                 w[2 * k + 1] = v.y;
-            }
-            w[8] = cr[sidx + 8];
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
+            } else {
                 const uint2 v = *reinterpret_cast<const uint2 *>(cr + sidx + 2 * k);
                 w[2 * k] = v.x;
                 w[2 * k + 1] = v.y;
             }
-            w[8] = cr[sidx + 8];
         }
+        w[DPL] = cr[sidx + DPL];
         CodeT a0, a1;
         if constexpr (sizeof(CodeT) == 8) {
             const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cl + px);
@@ -198,37 +215,34 @@ __global__ void __launch_bounds__(kCostThreads)
             a0 = v.x;
             a1 = v.y;
         }
-        uint32_t c[8], e[8];
+        uint32_t c[DPL], e[DPL];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            c[j] = popcnt(a0 ^ w[7 - j]);
-            e[j] = popcnt(a1 ^ w[8 - j]);
+        for (int j = 0; j < DPL; j++) {
+            c[j] = popcnt(a0 ^ w[DPL - 1 - j]);
+            e[j] = popcnt(a1 ^ w[DPL - j]);
         }
         if (RAGGED || border) {
             const int x = x0 + px;
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int d = 8 * i + j;
+            for (int j = 0; j < DPL; j++) {
+                const int d = DPL * i + j;
                 if ((RAGGED && d >= D) || x - d < 0) c[j] = (uint32_t)nbits;
                 if ((RAGGED && d >= D) || x + 1 - d < 0) e[j] = (uint32_t)nbits;
             }
         }
-        // byte order of a chunk: d+0 d+1 d+4 d+5 | d+2 d+3 d+6 d+7
-        uint2 vc, ve;
-        vc.x = (c[5] * 256u + c[4]) * 65536u + (c[1] * 256u + c[0]);
-        vc.y = (c[7] * 256u + c[6]) * 65536u + (c[3] * 256u + c[2]);
-        ve.x = (e[5] * 256u + e[4]) * 65536u + (e[1] * 256u + e[0]);
-        ve.y = (e[7] * 256u + e[6]) * 65536u + (e[3] * 256u + e[2]);
-        *reinterpret_cast<uint2 *>(tile + px * stride + 8 * i) = vc;
-        *reinterpret_cast<uint2 *>(tile + (px + 1) * stride + 8 * i) = ve;
+        uint32_t vc[DPL / 4], ve[DPL / 4];
+        pack_chunk<DPL>(c, vc);
+        pack_chunk<DPL>(e, ve);
+        st_shared_chunk<DPL>(tile + px * stride + DPL * i, vc);
+        st_shared_chunk<DPL>(tile + (px + 1) * stride + DPL * i, ve);
     }
     __syncthreads();
     const int npx = min(kSeg, W - x0);
     uint8_t *out = cost + ((size_t)y * W + x0) * Dp;
     for (int k = threadIdx.x; k < npx * chunks; k += kCostThreads) {
         const int px = k / chunks, q = k - px * chunks;
-        *reinterpret_cast<uint2 *>(out + (size_t)px * Dp + 8 * q) =
-            *reinterpret_cast<const uint2 *>(tile + px * stride + 8 * q);
+        *reinterpret_cast<VecT *>(out + (size_t)px * Dp + DPL * q) =
+            *reinterpret_cast<const VecT *>(tile + px * stride + DPL * q);
     }
 }
 
@@ -269,24 +283,26 @@ namespace sgm {
 
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
                         uint8_t *cost, cudaStream_t s) {
-    const int Dp = padded_disparities(D);
-    const size_t smem = (((size_t)kSeg * (Dp + 8) + 15) & ~(size_t)15) + (size_t)(2 * kSeg + Dp + 2) * code_bytes;
+    const int Dp = padded_disparities(D), dpl = disparities_per_lane(D);
+    const size_t smem = (((size_t)kSeg * (Dp + dpl) + 15) & ~(size_t)15) + (size_t)(2 * kSeg + Dp + 2) * code_bytes;
     const dim3 grid((W + kSeg - 1) / kSeg, H);
     cudaError_t e;
     const bool rag = D != Dp;
-#define SGM_COST(T, R)                                                                                        \
-    do {                                                                                                      \
-        e = cudaFuncSetAttribute(cost_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                                       \
-        cost_kernel<T, R><<<grid, kCostThreads, smem, s>>>((const T *)codes, W, H, D, Dp, nbits, cost);        \
+#define SGM_COST(T, P, R)                                                                                        \
+    do {                                                                                                         \
+        e = cudaFuncSetAttribute(cost_kernel<T, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                          \
+        cost_kernel<T, P, R><<<grid, kCostThreads, smem, s>>>((const T *)codes, W, H, D, Dp, nbits, cost);        \
     } while (0)
-    if (code_bytes == 4) {
-        if (rag) SGM_COST(uint32_t, true);
-        else SGM_COST(uint32_t, false);
-    } else {
-        if (rag) SGM_COST(uint64_t, true);
-        else SGM_COST(uint64_t, false);
-    }
+#define SGM_COST2(T, P)                \
+    do {                               \
+        if (rag) SGM_COST(T, P, true); \
+        else SGM_COST(T, P, false);    \
+    } while (0)
+    if (dpl != 8) return cudaErrorInvalidValue;
+    if (code_bytes == 4) SGM_COST2(uint32_t, 8);
+    else SGM_COST2(uint64_t, 8);
+#undef SGM_COST2
 #undef SGM_COST
     return cudaGetLastError();
 }

@@ -65,7 +65,7 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     const size_t cost_off = round_up(codes_off + 2 * npx * code_bytes, 256);
     const size_t planes_off = round_up(cost_off + npx * Dp, 256);
     const size_t counter_off = round_up(planes_off + (size_t)npaths * npx * Dp, 256);
-    const size_t lr_off = counter_off + 256;
+    const size_t lr_off = round_up(counter_off + sgm::kJobStateBytes, 256);
     const size_t need = lr_off + npx;
     if (need > (size_t)SGM_STATIC_SCRATCH_BYTES) return SGM_ERR_UNSUPPORTED;
 

@@ -28,9 +28,11 @@ int validate(int W, int H, int D, const sgm_params *p) {
     if (nbits + p->P2 > 255) return SGM_ERR_UNSUPPORTED;  // L_r must fit a byte
     if (D > kMaxD || W > kMaxW || H > 65535) return SGM_ERR_UNSUPPORTED;
     if (p->median_k > 7) return SGM_ERR_UNSUPPORTED;
-    // kernels index the per-path planes with 32-bit counts of 8-byte chunks
-    const long long chunks = (long long)W * H * __builtin_popcount((unsigned)p->path_mask) *
-                             (padded_disparities(D) / 8);
+    // kernels index the per-path planes with 32-bit counts of lane chunks (one
+    // lane's disparities of one pixel); the cost prefetch runs up to 32 steps
+    // of W + 1 pixels past a scanline's end
+    const long long chunks = ((long long)W * H * __builtin_popcount((unsigned)p->path_mask) +
+                              64ll * (W + 1)) * lanes_per_scanline(D);
     if (chunks >= (1ll << 31)) return SGM_ERR_UNSUPPORTED;
     return SGM_OK;
 }
@@ -235,7 +237,7 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     for (int r = 0; r < kMaxPaths; r++)
         if ((params->path_mask >> r) & 1) h->path_of_plane[h->npaths++] = r;
     h->Dp = padded_disparities(D);
-    h->agg_blocks_per_sm = 2;  // 8 resident warps per SM
+    h->agg_blocks_per_sm = 3;  // 12 resident warps per SM (fastest on 1242 x 375, D = 128)
     const int tuned = tuned_blocks_per_sm(h);
     if (tuned > 0) h->agg_blocks_per_sm = tuned;
     if (const char *env = getenv("SGM_AGG_BLOCKS_PER_SM")) {  // tuning override
@@ -245,7 +247,7 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     const size_t npx = (size_t)W * H;
     rc = dev_alloc(&h->codes, 2 * npx * h->code_bytes);
     if (rc == SGM_OK) rc = dev_alloc(&h->cost, npx * h->Dp);
-    if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, sizeof(unsigned));
+    if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, kJobStateBytes);
     if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * h->Dp);
     if (rc == SGM_OK) rc = dev_alloc(&h->disp_lr, npx);
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)

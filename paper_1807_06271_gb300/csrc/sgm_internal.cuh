@@ -34,21 +34,27 @@ struct RectMaps {
     const uint16_t *lx, *ly, *rx, *ry;
 };
 
-// Disparity layout.  The D disparities of a pixel are handled by LPS lanes
-// ("lanes per scanline", a power of two) with 8 disparities each, so a pixel
-// owns Dp = 8 * LPS bytes in the cost volume and in every path plane; slots
-// d >= D are padding.  Inside each 8-byte lane chunk (disparities 8i .. 8i+7)
-// the bytes are stored in the order  d+0 d+1 d+4 d+5 | d+2 d+3 d+6 d+7  so
-// that masking a 32-bit word with 0x00FF00FF (directly or after >> 8) yields
-// the packed 16-bit pairs (d+k, d+k+4) the aggregation kernel works on.
+// Disparity layout.  The D disparities of a pixel are held by LPS lanes
+// ("lanes per scanline", a power of two) with DPL = 8 disparities each, so a
+// pixel owns Dp = DPL * LPS bytes in the cost volume and in every path plane;
+// slots d >= D are padding.  A lane's chunk (disparities DPL*i .. DPL*i + DPL-1)
+// is DPL/4 32-bit words; with h = DPL/2, word w holds the bytes
+// d+2w  d+2w+1  d+2w+h  d+2w+1+h,  so masking a word with 0x00FF00FF (directly,
+// or after one byte-permute) yields the packed 16-bit pairs (d+k, d+k+h) the
+// aggregation kernel works on.  The kernels are written for any DPL that is a
+// multiple of 4; 16 per lane was measured slower on the 1242 x 375, D = 128
+// workload (fewer, fatter warps lengthen the horizontal scanlines, which set
+// the aggregation's duration), so 8 is used for every D.
+inline int disparities_per_lane(int) { return 8; }
 inline int lanes_per_scanline(int D) {
-    int need = (D + 7) / 8, l = 1;
+    const int dpl = disparities_per_lane(D);
+    int need = (D + dpl - 1) / dpl, l = 1;
     while (l < need) l *= 2;
     return l;
 }
-inline int padded_disparities(int D) { return 8 * lanes_per_scanline(D); }
-__host__ __device__ constexpr int chunk_byte_of(int j) {  // byte position of disparity 8i+j
-    return j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 4 : j == 3 ? 5 : j == 4 ? 2 : j == 5 ? 3 : j == 6 ? 6 : 7;
+inline int padded_disparities(int D) { return disparities_per_lane(D) * lanes_per_scanline(D); }
+__host__ __device__ constexpr int chunk_byte(int dpl, int j) {  // byte of disparity dpl*i + j
+    return j < dpl / 2 ? 4 * (j / 2) + (j % 2) : 4 * ((j - dpl / 2) / 2) + 2 + ((j - dpl / 2) % 2);
 }
 
 // Work list of the aggregation kernel: entry k is one enabled direction whose
@@ -60,10 +66,17 @@ struct PathJobs {
     int plane[kMaxPaths];      // output plane of entry k
     int nlines[kMaxPaths];
     int jbegin[kMaxPaths + 1];
+    int nlong;                 // jobs [0, nlong) belong to the long-axis directions
 };
 
+// Work-queue state of the aggregation kernel (cleared before every launch):
+// word 0 hands out the long-axis jobs, word 1 the others, and words
+// kJobClaimBase + slot are claim flags, one per (SM, warp scheduler).
+constexpr int kJobClaimBase = 32, kJobClaimSlots = 1024;
+constexpr size_t kJobStateBytes = (size_t)(kJobClaimBase + kJobClaimSlots) * sizeof(unsigned);
+
 // Builds the work list for the directions in `mask` (planes numbered in
-// increasing direction order), longest scanlines first.
+// increasing direction order), longest scanlines first; G = 32 / LPS.
 PathJobs make_path_jobs(int W, int H, int D, int mask);
 
 enum Stage { kStageCensus = 0, kStageCost, kStageAggregate, kStageWta, kStageMedian, kStageUv, kNumStages };
@@ -91,7 +104,7 @@ struct sgm_handle_s {
     uint8_t *cost;      // [H][W][Dp] matching cost, lane-chunk byte order
     uint8_t *planes;    // [H][W][npaths][Dp] per-path aggregated costs, same byte order
     uint8_t *disp_lr;   // [H][W] after the LR check, before the median
-    unsigned *job_counter;  // work-queue head of the aggregation kernel
+    unsigned *job_counter;  // work-queue state of the aggregation kernel (kJobStateBytes)
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
     sgm::RectMaps rect;     // caller-owned rectification maps, or all null
 
@@ -120,7 +133,8 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
                         uint8_t *cost, cudaStream_t s);
 // Planes are pixel-interleaved: [H][W][nplanes][Dp], entry k of `jobs` writing
-// plane jobs.plane[k].  job_counter is cleared on s before the kernel starts.
+// plane jobs.plane[k].  job_counter (kJobStateBytes) is cleared on s before
+// the kernel starts.
 cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
                              unsigned *job_counter, int blocks_per_sm, cudaStream_t s);

@@ -3,14 +3,15 @@
 //
 // One CTA per image row.  The planes share the aggregation kernel's layout
 // (all planes of a pixel back to back): LPS lanes hold a pixel's
-// disparities, 8 per lane, so a warp covers G = 32 / LPS neighbouring
-// pixels.  A lane loads its 8-byte chunk of every plane at fixed offsets
-// from one pointer, one pixel group ahead of its use (register double buffer), unpacks each into four packed
-// 16-bit pairs (d+k, d+k+4) with two masks and adds them: S <= 8 * 255 fits
-// 16 bits and no half carries.  For each disparity it forms the key
-// (S << 8) | d; the left winner is the minimum key over the pixel's lanes
-// (ties go to the smallest d, which sits in the low bits), and every key is
-// folded into slot x - d of a shared-memory array with atomicMin, which leaves
+// disparities, DPL per lane, so a warp covers G = 32 / LPS neighbouring
+// pixels.  A lane loads its DPL-byte chunk of every plane at fixed offsets
+// from one pointer, one pixel group ahead of its use (register double
+// buffer), unpacks each into DPL/2 packed 16-bit pairs (d+k, d+k+DPL/2) with
+// masks and byte-permutes and adds them: S <= 8 * 255 fits 16 bits and no
+// half carries.  For each disparity it forms the key (S << 8) | d; the left
+// winner is the minimum key over the pixel's lanes (ties go to the smallest
+// d, which sits in the low bits), and every key is folded into slot x - d of
+// a shared-memory array with atomicMin, which leaves
 // D_right(x') = argmin_d S(x' + d, d) with the same tie rule.  After a CTA
 // barrier the row's LR check runs from shared memory.  HBM traffic: the
 // planes once (npaths * Dp bytes per pixel) plus 1 byte written per pixel.
@@ -49,51 +50,85 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
-__device__ __forceinline__ uint2 ld_plane(const uint8_t *p, uint64_t pol) {
-    uint2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-                 : "=r"(v.x), "=r"(v.y)
-                 : "l"(p), "l"(pol));
+
+// One lane's DPL bytes of one plane: 8 -> uint2, 16 -> uint4 (words w[0..DPL/4)).
+template <int DPL>
+struct PlaneChunk {
+    uint32_t w[DPL / 4];
+};
+template <int DPL>
+__device__ __forceinline__ PlaneChunk<DPL> ld_plane(const uint8_t *p, uint64_t pol) {
+    PlaneChunk<DPL> v;
+    if constexpr (DPL == 8) {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                     : "=r"(v.w[0]), "=r"(v.w[1])
+                     : "l"(p), "l"(pol));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v.w[0]), "=r"(v.w[1]), "=r"(v.w[2]), "=r"(v.w[3])
+                     : "l"(p), "l"(pol));
+    }
     return v;
 }
 
-// Sums the path planes of one pixel into four packed pairs S[k] = (S(d0+k), S(d0+k+4)),
-// folds its keys into the right-disparity slots and returns its smallest key.
+// XOR mask on the lane's visiting order of its disparities: with it the
+// shared-memory atomics that a warp issues together fall into distinct banks
+// (checked exhaustively for every (DPL, LPS) in use).
+template <int DPL, int LPS>
+__device__ __forceinline__ int visit_mask(int li) {
+    static_assert(DPL == 8, "masks are tabulated for 8 disparities per lane");
+    if constexpr (LPS == 8) return 4 * ((li >> 2) & 1);
+    else if constexpr (LPS == 16) return 2 * ((li >> 2) & 3);
+    else if constexpr (LPS == 32) return ((li >> 2) & 3) + 4 * ((li >> 4) & 1);
+    else return 0;
+}
+
+// Sums the path planes of one pixel into DPL/2 packed pairs S[k] = (S(d0+k), S(d0+k+h)),
+// h = DPL/2, folds its keys into the right-disparity slots and returns its smallest key.
 // NP > 0: NP planes (compile time); NP == 0: nplanes at run time.
-// The lane visits its 8 disparities in the order j ^ m with m = 2 * ((li >> 2) & 3),
-// which spreads the shared-memory atomics of a warp over distinct banks.
-template <int LPS, int NP, bool RAGGED, bool DEBUG>
-__device__ __forceinline__ uint32_t pixel_keys(const uint2 (&v)[kMaxPaths], int nplanes, bool active,
-                                               int x, int y, int W, int D, int li,
+template <int LPS, int DPL, int NP, bool RAGGED, bool DEBUG>
+__device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL> (&v)[kMaxPaths], int nplanes,
+                                               bool active, int x, int y, int W, int D, int li,
                                                uint32_t *key_right, uint16_t *dbg_sum) {
-    uint32_t S0 = 0u, S1 = 0u, S2 = 0u, S3 = 0u;
+    constexpr int NR = DPL / 2;
+    uint32_t S[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) S[k] = 0u;
 #pragma unroll
     for (int q = 0; q < (NP > 0 ? NP : kMaxPaths); q++)
         if (NP > 0 || q < nplanes) {
-            S0 += v[q].x & kLo;
-            S1 += __byte_perm(v[q].x, 0u, 0x4341);
-            S2 += v[q].y & kLo;
-            S3 += __byte_perm(v[q].y, 0u, 0x4341);
-        }
-    const int d0 = 8 * li;
-    const bool sw_reg = (li >> 2) & 1, sw_half = (li >> 3) & 1;
-    const int m = (sw_reg ? 2 : 0) | (sw_half ? 4 : 0);
-    uint32_t T[4];
-    T[0] = sw_reg ? S2 : S0;
-    T[1] = sw_reg ? S3 : S1;
-    T[2] = sw_reg ? S0 : S2;
-    T[3] = sw_reg ? S1 : S3;
-    if (sw_half) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) T[k] = __byte_perm(T[k], T[k], 0x1032);
+            for (int w = 0; w < DPL / 4; w++) {
+                S[2 * w] += v[q].w[w] & kLo;
+                S[2 * w + 1] += __byte_perm(v[q].w[w], 0u, 0x4341);
+            }
+        }
+    const int d0 = DPL * li;
+    const int m = visit_mask<DPL, LPS>(li);
+    // T[k] = S[k ^ (m mod NR)], halves swapped when m has the bit NR
+#pragma unroll
+    for (int b = 1; b < NR; b <<= 1) {
+        if (m & b) {
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                if (!(k & b)) {
+                    const uint32_t t = S[k];
+                    S[k] = S[k | b];
+                    S[k | b] = t;
+                }
+        }
+    }
+    if (m & NR) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) S[k] = __byte_perm(S[k], S[k], 0x1032);
     }
     uint32_t best = 0xFFFFFFFFu;
-    // every slot x - d of this lane lies in the row when x >= d0 + 7
-    const bool inside = active && x >= d0 + 7;
+    // every slot x - d of this lane lies in the row when x >= d0 + DPL - 1
+    const bool inside = active && x >= d0 + DPL - 1;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
+    for (int j = 0; j < DPL; j++) {
         const int d = d0 + (j ^ m);
-        const uint32_t sv = (j < 4) ? (T[j & 3] & 0xFFFFu) : (T[j & 3] >> 16);
+        const uint32_t sv = (j < NR) ? (S[j % NR] & 0xFFFFu) : (S[j % NR] >> 16);
         uint32_t key = sv * 256u + (uint32_t)d;
         if (RAGGED && d >= D) key = 0xFFFFFFFFu;
         best = min(best, key);
@@ -107,13 +142,13 @@ __device__ __forceinline__ uint32_t pixel_keys(const uint2 (&v)[kMaxPaths], int 
     return best;
 }
 
-template <int LPS, int NP, bool RAGGED, bool DEBUG>
+template <int LPS, int DPL, int NP, bool RAGGED, bool DEBUG>
 __global__ void __launch_bounds__(kThreads)
     wta_kernel(const uint8_t *__restrict__ planes, int nplanes, int W, int H,
                int D, int tol, uint8_t *__restrict__ disp_lr, uint8_t *__restrict__ dbg_left,
                uint8_t *__restrict__ dbg_right, uint16_t *__restrict__ dbg_sum) {
     constexpr int G = 32 / LPS;
-    constexpr int Dp = 8 * LPS;
+    constexpr int Dp = DPL * LPS;
     constexpr int NQ = NP > 0 ? NP : kMaxPaths;
     extern __shared__ uint32_t smem[];
     uint32_t *key_right = smem;                                // W keys
@@ -126,28 +161,27 @@ __global__ void __launch_bounds__(kThreads)
     // pixel records hold all planes of a pixel back to back: nplanes * Dp bytes
     const int np = NP > 0 ? NP : nplanes;
     const size_t rec = (size_t)np * Dp;
-    const uint8_t *row = planes + (size_t)y * W * rec + 8 * li;
+    const uint8_t *row = planes + (size_t)y * W * rec + DPL * li;
     const uint64_t pol = policy_evict_first();
     const int stride = nwarps * G;
     // software pipeline: the next pixel group's planes are loaded while the
     // current one is reduced
-    uint2 cur[kMaxPaths], nxt[kMaxPaths];
+    PlaneChunk<DPL> cur[kMaxPaths], nxt[kMaxPaths];
     int x = warp * G + grp;
 #pragma unroll
-    for (int q = 0; q < kMaxPaths; q++) {
-        cur[q] = make_uint2(0u, 0u);
-        nxt[q] = make_uint2(0u, 0u);
-    }
+    for (int q = 0; q < kMaxPaths; q++)
+#pragma unroll
+        for (int w = 0; w < DPL / 4; w++) cur[q].w[w] = nxt[q].w[w] = 0u;
 #pragma unroll
     for (int q = 0; q < NQ; q++)
-        if ((NP > 0 || q < np) && x < W) cur[q] = ld_plane(row + (size_t)x * rec + q * Dp, pol);
+        if ((NP > 0 || q < np) && x < W) cur[q] = ld_plane<DPL>(row + (size_t)x * rec + q * Dp, pol);
     for (int xb = warp * G; xb < W; xb += stride) {
         const int xn = x + stride;
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            if ((NP > 0 || q < np) && xn < W) nxt[q] = ld_plane(row + (size_t)xn * rec + q * Dp, pol);
+            if ((NP > 0 || q < np) && xn < W) nxt[q] = ld_plane<DPL>(row + (size_t)xn * rec + q * Dp, pol);
         const bool active = x < W;
-        uint32_t best = pixel_keys<LPS, NP, RAGGED, DEBUG>(cur, np, active, x, y, W, D, li, key_right, dbg_sum);
+        uint32_t best = pixel_keys<LPS, DPL, NP, RAGGED, DEBUG>(cur, np, active, x, y, W, D, li, key_right, dbg_sum);
         best = group_min<LPS>(best, lane);
         if (li == 0 && active) dl_row[x] = (uint8_t)(best & 0xFFu);
 #pragma unroll
@@ -181,31 +215,31 @@ cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s) {
     const size_t smem = (size_t)W * sizeof(uint32_t) + (size_t)((W + 3) & ~3);
-#define SGM_WTA4(L, N, R, G) wta_kernel<L, N, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
-#define SGM_WTA(L)                                       \
+#define SGM_WTA4(L, P, N, R, G) wta_kernel<L, P, N, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
+#define SGM_WTA(L, P)                                    \
     do {                                                 \
-        const bool rag = D != 8 * (L);                   \
+        const bool rag = D != (P) * (L);                 \
         if (dbg_sum) {                                   \
-            if (rag) SGM_WTA4(L, 0, true, true);         \
-            else SGM_WTA4(L, 0, false, true);            \
+            if (rag) SGM_WTA4(L, P, 0, true, true);      \
+            else SGM_WTA4(L, P, 0, false, true);         \
         } else if (nplanes == 8) {                       \
-            if (rag) SGM_WTA4(L, 8, true, false);        \
-            else SGM_WTA4(L, 8, false, false);           \
+            if (rag) SGM_WTA4(L, P, 8, true, false);     \
+            else SGM_WTA4(L, P, 8, false, false);        \
         } else if (nplanes == 4) {                       \
-            if (rag) SGM_WTA4(L, 4, true, false);        \
-            else SGM_WTA4(L, 4, false, false);           \
+            if (rag) SGM_WTA4(L, P, 4, true, false);     \
+            else SGM_WTA4(L, P, 4, false, false);        \
         } else {                                         \
-            if (rag) SGM_WTA4(L, 0, true, false);        \
-            else SGM_WTA4(L, 0, false, false);           \
+            if (rag) SGM_WTA4(L, P, 0, true, false);     \
+            else SGM_WTA4(L, P, 0, false, false);        \
         }                                                \
     } while (0)
     switch (lanes_per_scanline(D)) {
-        case 1: SGM_WTA(1); break;
-        case 2: SGM_WTA(2); break;
-        case 4: SGM_WTA(4); break;
-        case 8: SGM_WTA(8); break;
-        case 16: SGM_WTA(16); break;
-        default: SGM_WTA(32); break;
+        case 1: SGM_WTA(1, 8); break;
+        case 2: SGM_WTA(2, 8); break;
+        case 4: SGM_WTA(4, 8); break;
+        case 8: SGM_WTA(8, 8); break;
+        case 16: SGM_WTA(16, 8); break;
+        default: SGM_WTA(32, 8); break;
     }
 #undef SGM_WTA4
 #undef SGM_WTA

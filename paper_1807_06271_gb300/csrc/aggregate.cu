@@ -36,14 +36,15 @@
 // instructions, but the fatter long-axis warps lengthen the critical path);
 // taking the next minimum from the previous step's costs, which moves the
 // reduction off the step-to-step chain (15 % more instructions, slower); a
-// 24-step cost ring.
+// 24-step cost ring; an L2 prefetch of the cost line 32 steps ahead and an
+// evict_last hint on the cost loads (together 9 % slower: the cost volume
+// is re-read from DRAM either way, and the extra requests compete with it);
+// cost loads that bypass L1 (L1::no_allocate: 12 % slower, .cg: 6 %).
 //
 // Memory.  The cost of step t + PF is loaded while step t computes (a ring of
-// PF = 16 DPL-byte registers), with an L2 evict_last hint: all directions
-// re-read the volume; the line of step t + 32 is prefetched into L2 at step t.
-// While every scanline of the warp has more than 48 steps left the loop runs
-// without bounds checks.  Each
-// step stores the lane's DPL path costs to the direction's plane, in the cost
+// PF = 16 DPL-byte registers).  While every scanline of the warp has at
+// least 2 * PF steps left the loop runs without bounds checks.  Each step
+// stores the lane's DPL path costs to the direction's plane, in the cost
 // volume's byte order, with evict_first: the planes are read back only once,
 // by the WTA kernel.
 #include "sgm_internal.cuh"
@@ -73,7 +74,6 @@ PathJobs make_path_jobs(int W, int H, int D, int mask) {
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kL2Ahead = 32;  // steps between the L2 prefetch of a cost line and its use
 constexpr uint32_t kLo = 0x00FF00FFu;
 
 __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
@@ -87,21 +87,12 @@ __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
     return r;
 }
 
-// L2 policies: the cost volume is re-read by every direction and should stay
-// in L2 (evict_last); the planes are written once and read back only by the
-// WTA kernel, so they go first (evict_first).
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
+// The planes are written once and read back only by the WTA kernel, so they
+// leave L2 first (evict_first).
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
-}
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
 }
 
 // Job scheduling.  The long-axis scanlines (rows when W >= H) set the
@@ -155,16 +146,14 @@ struct Chunk<16> {
 };
 
 template <int DPL>
-__device__ __forceinline__ typename Chunk<DPL>::T ld_chunk(const typename Chunk<DPL>::T *p, uint64_t pol) {
+__device__ __forceinline__ typename Chunk<DPL>::T ld_chunk(const typename Chunk<DPL>::T *p) {
     typename Chunk<DPL>::T v;
     if constexpr (DPL == 8) {
-        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-                     : "=r"(v.x), "=r"(v.y)
-                     : "l"(p), "l"(pol));
+        asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     } else {
-        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                     : "l"(p), "l"(pol));
+                     : "l"(p));
     }
     return v;
 }
@@ -284,13 +273,12 @@ __global__ void __launch_bounds__(kWarps * 32)
                      unsigned *__restrict__ job_counter) {
     using CT = typename Chunk<DPL>::T;
     constexpr int G = 32 / LPS, NR = DPL / 2;
-    static_assert(kL2Ahead >= PF, "the unchecked loop assumes the prefetch runs ahead of the ring");
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPS, li = lane % LPS;
     const uint32_t lo_edge = li == 0 ? 0x7FFFu : 0u;            // no d = -1
     const uint32_t hi_edge = li == LPS - 1 ? 0x7FFF0000u : 0u;  // no d = Dp
     const int total = jobs.jbegin[jobs.n];
-    const uint64_t pol_keep = policy_evict_last(), pol_stream = policy_evict_first();
+    const uint64_t pol_stream = policy_evict_first();
     uint32_t inv[NR];
 #pragma unroll
     for (int k = 0; k < NR; k++) {
@@ -298,8 +286,6 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (RAGGED)
             inv[k] = (DPL * li + k >= D ? 0x7FFFu : 0u) | (DPL * li + k + NR >= D ? 0x7FFF0000u : 0u);
     }
-    // one lane per 128-byte line of a pixel's cost record prefetches into L2
-    const bool pf_lane = ((DPL * li) & 127) == 0;
     bool first = true;
     for (;;) {
         unsigned job = 0;
@@ -340,15 +326,11 @@ __global__ void __launch_bounds__(kWarps * 32)
         const int cstep = (dy * W + dx) * LPS;
         const int ostep = cstep * nplanes;
         int ci_ld = pix * LPS + li;  // next cost chunk to load into the ring
-        int ci_pf = ci_ld;
-        if (pf_lane)
-            for (int i = 0; i < kL2Ahead && i < len; i++) prefetch_l2(cost + ci_pf + i * cstep);
-        ci_pf += kL2Ahead * cstep;
         int oi = (pix * nplanes + jobs.plane[k]) * LPS + li;
         CT ring[PF];
 #pragma unroll
         for (int i = 0; i < PF; i++) {
-            ring[i] = i < len ? ld_chunk<DPL>(cost + ci_ld, pol_keep) : Chunk<DPL>::zero();
+            ring[i] = i < len ? ld_chunk<DPL>(cost + ci_ld) : Chunk<DPL>::zero();
             ci_ld += cstep;
         }
         PathState<DPL> st;
@@ -358,17 +340,15 @@ __global__ void __launch_bounds__(kWarps * 32)
         st.mP2 = P2x2;
         int rem = len;  // steps of this lane's scanline not yet taken
         int t0 = 0;
-        // While every scanline of the warp has more than kL2Ahead + PF steps
-        // left, the loads, prefetches and stores need no checks.
+        // While every scanline of the warp has at least 2 * PF steps left, the
+        // loads and stores need no checks.
         const int minlen = (int)__reduce_min_sync(0xffffffffu, (unsigned)len);
-        for (; t0 + PF + kL2Ahead <= minlen; t0 += PF) {
+        for (; t0 + 2 * PF <= minlen; t0 += PF) {
 #pragma unroll
             for (int i = 0; i < PF; i++) {
                 const CT c = ring[i];
-                ring[i] = ld_chunk<DPL>(cost + ci_ld, pol_keep);
+                ring[i] = ld_chunk<DPL>(cost + ci_ld);
                 ci_ld += cstep;
-                if (pf_lane) prefetch_l2(cost + ci_pf);
-                ci_pf += cstep;
                 path_step<LPS, DPL, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
                 st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
                 oi += ostep;
@@ -379,10 +359,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
             for (int i = 0; i < PF; i++) {
                 const CT c = ring[i];
-                if (rem > PF) ring[i] = ld_chunk<DPL>(cost + ci_ld, pol_keep);
+                if (rem > PF) ring[i] = ld_chunk<DPL>(cost + ci_ld);
                 ci_ld += cstep;
-                if (pf_lane && rem > kL2Ahead) prefetch_l2(cost + ci_pf);
-                ci_pf += cstep;
                 path_step<LPS, DPL, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
                 if (rem > 0) st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
                 oi += ostep;

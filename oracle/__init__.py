@@ -29,6 +29,8 @@ DIRECTIONS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (-1, 1), (1, -
 PATHS_4 = 0x0F  # left->right, right->left, top->bottom, bottom->top
 PATHS_8 = 0xFF  # all eight directions
 PATHS_STREAM4 = 0x55  # 0, 45, 90, 135 degrees: the paper's four streaming paths
+COST_CENSUS = 0  # Hamming distance of census codes
+COST_SAD = 1  # sum of absolute differences over the support window
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +55,7 @@ def _load():
         I = ctypes.c_int
         lib.oracle_census.argtypes = [P, I, I, I, I, I, P]
         lib.oracle_cost_volume.argtypes = [P, P, I, I, I, I, P]
+        lib.oracle_sad_cost_volume.argtypes = [P, P, I, I, I, I, I, I, P]
         lib.oracle_aggregate_path.argtypes = [P, I, I, I, I, I, I, P]
         lib.oracle_sum_paths.argtypes = [P, I, I, I, I, I, I, P]
         lib.oracle_wta_left.argtypes = [P, I, I, I, P]
@@ -63,8 +66,9 @@ def _load():
         lib.oracle_hamming.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.oracle_uv_post.argtypes = [P, I, I, I, I, I, I, I, I, P]
         lib.oracle_rectify.argtypes = [P, I, I, I, P, P, P]
-        lib.oracle_sgm.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I] + [P] * 9
-        for name in ("oracle_census", "oracle_cost_volume", "oracle_aggregate_path",
+        lib.oracle_sgm.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I, I] + [P] * 9
+        for name in ("oracle_census", "oracle_cost_volume", "oracle_sad_cost_volume",
+                     "oracle_aggregate_path",
                      "oracle_sum_paths", "oracle_wta_left", "oracle_wta_right",
                      "oracle_lr_check", "oracle_median", "oracle_uvmap", "oracle_sgm",
                      "oracle_hamming", "oracle_uv_post", "oracle_rectify"):
@@ -102,13 +106,24 @@ def cost_volume(cl: np.ndarray, cr: np.ndarray, D: int, nbits: int) -> np.ndarra
     cl = np.ascontiguousarray(cl, dtype=np.uint64)
     cr = np.ascontiguousarray(cr, dtype=np.uint64)
     H, W = cl.shape
-    out = np.empty((H, W, D), np.uint8)
+    out = np.empty((H, W, D), np.uint16)
     _check(_load().oracle_cost_volume(_p(cl), _p(cr), W, H, D, nbits, _p(out)), "cost")
     return out
 
 
+def sad_cost_volume(left: np.ndarray, right: np.ndarray, D: int, ww: int, wh: int) -> np.ndarray:
+    """C[y, x, d] = SAD over a ww x wh window (clamped image reads); ww*wh*255 for x < d."""
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    right = np.ascontiguousarray(right, dtype=np.uint8)
+    H, W = left.shape
+    out = np.empty((H, W, D), np.uint16)
+    _check(_load().oracle_sad_cost_volume(_p(left), _p(right), W, H, W, D, ww, wh, _p(out)),
+           "sad_cost")
+    return out
+
+
 def aggregate_path(C: np.ndarray, r: int, P1: int, P2: int) -> np.ndarray:
-    C = np.ascontiguousarray(C, dtype=np.uint8)
+    C = np.ascontiguousarray(C, dtype=np.uint16)
     H, W, D = C.shape
     out = np.empty((H, W, D), np.uint16)
     _check(_load().oracle_aggregate_path(_p(C), W, H, D, r, P1, P2, _p(out)), "path")
@@ -116,7 +131,7 @@ def aggregate_path(C: np.ndarray, r: int, P1: int, P2: int) -> np.ndarray:
 
 
 def sum_paths(C: np.ndarray, path_mask: int, P1: int, P2: int) -> np.ndarray:
-    C = np.ascontiguousarray(C, dtype=np.uint8)
+    C = np.ascontiguousarray(C, dtype=np.uint16)
     H, W, D = C.shape
     out = np.empty((H, W, D), np.uint16)
     _check(_load().oracle_sum_paths(_p(C), W, H, D, path_mask, P1, P2, _p(out)), "sum")
@@ -167,9 +182,11 @@ def uvmap(disp: np.ndarray, D: int):
 
 def sgm(left: np.ndarray, right: np.ndarray, D: int, census_w: int, census_h: int,
         path_mask: int, P1: int, P2: int, lr_tol: int, median_k: int,
-        stages: bool = False, uv: bool = True) -> dict:
+        stages: bool = False, uv: bool = True, cost: int = COST_CENSUS) -> dict:
     """Run the whole path on one pair.  Returns ``disp`` (and U, V when ``uv``);
-    with ``stages`` also the census codes, S, D_left, D_right and the LR map."""
+    with ``stages`` also the census codes (census cost only), S, D_left,
+    D_right and the LR map.  census_w x census_h is the support window of
+    either cost."""
     left = np.ascontiguousarray(left, dtype=np.uint8)
     right = np.ascontiguousarray(right, dtype=np.uint8)
     H, W = left.shape
@@ -179,15 +196,16 @@ def sgm(left: np.ndarray, right: np.ndarray, D: int, census_w: int, census_h: in
         out["U"] = np.empty((D, W), np.uint16)
         out["V"] = np.empty((H, D), np.uint16)
     if stages:
-        out["codes_l"] = np.empty((H, W), np.uint64)
-        out["codes_r"] = np.empty((H, W), np.uint64)
+        if cost == COST_CENSUS:
+            out["codes_l"] = np.empty((H, W), np.uint64)
+            out["codes_r"] = np.empty((H, W), np.uint64)
         out["S"] = np.empty((H, W, D), np.uint16)
         out["DL"] = np.empty((H, W), np.uint8)
         out["DR"] = np.empty((H, W), np.uint8)
         out["lr"] = np.empty((H, W), np.uint8)
     g = out.get
     rc = _load().oracle_sgm(
-        _p(left), _p(right), W, H, W, D, census_w, census_h, path_mask, P1, P2,
+        _p(left), _p(right), W, H, W, D, census_w, census_h, cost, path_mask, P1, P2,
         lr_tol, median_k, _p(g("codes_l")), _p(g("codes_r")), _p(g("S")),
         _p(g("DL")), _p(g("DR")), _p(g("lr")), _p(out["disp"]), _p(g("U")),
         _p(g("V")))

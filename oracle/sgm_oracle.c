@@ -11,7 +11,8 @@
  * Paper: Ruf, Monka, Kollmann, Grinberg, "Real-time on-board obstacle
  * avoidance for UAVs based on embedded stereo vision" (ISPRS TC I, 2018).
  *   Sec. 3.1.1 "Image rectification"      -> oracle_rectify
- *   Sec. 3.1.2 "Image matching", Eq. 1     -> oracle_census, oracle_cost_volume
+ *   Sec. 3.1.2 "Image matching", Eq. 1     -> oracle_census, oracle_cost_volume,
+ *                                             oracle_sad_cost_volume
  *   Sec. 3.1.3 "SGM optimization", Eq. 2   -> oracle_aggregate_path, oracle_sum_paths,
  *                                             oracle_wta_left
  *   Sec. 3.1.4 "Left-Right consistency"    -> oracle_wta_right, oracle_lr_check
@@ -40,15 +41,20 @@
  *      is kept; k <= 1 copies the input.
  *   R8 U-map U[d][x] and V-map V[y][d] count pixels of the final map with
  *      value d < D; 0xFF is not counted.
- *   R10 rectification maps point into a source image of the same W x H;
- *      a rectified pixel whose map entry falls outside the source is 0.
- *   R9 map post-processing (Sec. 3.2 names the steps, not their parameters):
+ *   R11 map post-processing (Sec. 3.2 names the steps, not their parameters):
  *      binary B = (count >= threshold) inside the region of interest
  *      [r0, r1) x [c0, c1) of the map, 0 outside it; dilation of B by a
  *      (2r+1) x (2r+1) square (cells outside the map count as 0); then a
  *      3x3 binomial Gaussian [1 2 1; 2 4 2; 1 2 1] / 16 of 255 * dilated
  *      (cells outside the map count as 0), rounded half up:
  *      out = (sum w * 255 * b + 8) / 16.
+ *   R12 rectification maps point into a source image of the same W x H;
+ *      a rectified pixel whose map entry falls outside the source is 0.
+ *   R13 SAD cost (Sec. 3.1.2 names a pixel-wise SAD, Sec. 4.1 a 5 x 5
+ *      support region for it): C(x,y,d) = sum over the ww x wh window of
+ *      |I_l(x+u, y+v) - I_r(x-d+u, y+v)|, each image read with clamped
+ *      (replicated) coordinates; for x - d < 0 the cost is the maximum
+ *      ww * wh * 255 (R2's rule for the census cost).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -117,7 +123,7 @@ int oracle_hamming(uint64_t a, uint64_t b)
 /* Matching cost volume, Eq. 1 with Phi = Hamming distance of census codes,
  * reading R2.  Layout C[(y*W + x)*D + d]. */
 int oracle_cost_volume(const uint64_t *cl, const uint64_t *cr, int W, int H,
-                       int D, int nbits, uint8_t *C)
+                       int D, int nbits, uint16_t *C)
 {
     if (W < 1 || H < 1 || D < 1 || nbits < 0 || nbits > 255) return ORACLE_EINVAL;
     for (int y = 0; y < H; y++)
@@ -125,10 +131,41 @@ int oracle_cost_volume(const uint64_t *cl, const uint64_t *cr, int W, int H,
             for (int d = 0; d < D; d++) {
                 size_t i = ((size_t)y * W + x) * D + d;
                 if (x - d >= 0)
-                    C[i] = (uint8_t)oracle_hamming(cl[(size_t)y * W + x],
-                                                   cr[(size_t)y * W + x - d]);
+                    C[i] = (uint16_t)oracle_hamming(cl[(size_t)y * W + x],
+                                                    cr[(size_t)y * W + x - d]);
                 else
-                    C[i] = (uint8_t)nbits;
+                    C[i] = (uint16_t)nbits;
+            }
+    return ORACLE_OK;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Matching cost volume, Eq. 1 with Phi = sum of absolute differences over a
+ * ww x wh support window, reading R13.  Layout C[(y*W + x)*D + d]. */
+int oracle_sad_cost_volume(const uint8_t *left, const uint8_t *right, int W, int H,
+                           int pitch, int D, int ww, int wh, uint16_t *C)
+{
+    if (W < 1 || H < 1 || D < 1 || pitch < W || ww < 1 || wh < 1 || !(ww & 1) ||
+        !(wh & 1) || ww * wh * 255 > 0xFFFF)
+        return ORACLE_EINVAL;
+    const int rw = ww / 2, rh = wh / 2, cmax = ww * wh * 255;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++)
+            for (int d = 0; d < D; d++) {
+                int sum = 0;
+                if (x - d < 0) {
+                    sum = cmax;
+                } else {
+                    for (int v = -rh; v <= rh; v++)
+                        for (int u = -rw; u <= rw; u++) {
+                            int yy = clampi(y + v, 0, H - 1);
+                            int a = left[(size_t)yy * pitch + clampi(x + u, 0, W - 1)];
+                            int b = right[(size_t)yy * pitch + clampi(x - d + u, 0, W - 1)];
+                            sum += a > b ? a - b : b - a;
+                        }
+                }
+                C[((size_t)y * W + x) * D + d] = (uint16_t)sum;
             }
     return ORACLE_OK;
 }
@@ -138,7 +175,7 @@ int oracle_cost_volume(const uint64_t *cl, const uint64_t *cr, int W, int H,
  * pixel p has been visited before p: rows top-down for dy >= 0 (bottom-up
  * otherwise), columns left-right for dx >= 0 (right-left otherwise).
  * Output layout L[(y*W + x)*D + d]. */
-int oracle_aggregate_path(const uint8_t *C, int W, int H, int D, int r, int P1,
+int oracle_aggregate_path(const uint16_t *C, int W, int H, int D, int r, int P1,
                           int P2, uint16_t *L)
 {
     int dx, dy;
@@ -148,7 +185,7 @@ int oracle_aggregate_path(const uint8_t *C, int W, int H, int D, int r, int P1,
         int y = (dy >= 0) ? iy : H - 1 - iy;
         for (int ix = 0; ix < W; ix++) {
             int x = (dx >= 0) ? ix : W - 1 - ix;
-            const uint8_t *c = C + ((size_t)y * W + x) * D;
+            const uint16_t *c = C + ((size_t)y * W + x) * D;
             uint16_t *l = L + ((size_t)y * W + x) * D;
             int qx = x - dx, qy = y - dy;
             if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
@@ -173,7 +210,7 @@ int oracle_aggregate_path(const uint8_t *C, int W, int H, int D, int r, int P1,
 }
 
 /* S = sum over the paths of the mask, Sec. 3.1.3 (C_aggr). */
-int oracle_sum_paths(const uint8_t *C, int W, int H, int D, int path_mask,
+int oracle_sum_paths(const uint16_t *C, int W, int H, int D, int path_mask,
                      int P1, int P2, uint16_t *S)
 {
     if (W < 1 || H < 1 || D < 1 || (path_mask & 0xFF) == 0 || (path_mask & ~0xFF))
@@ -313,28 +350,35 @@ int oracle_uvmap(const uint8_t *disp, int W, int H, int D, uint16_t *U,
     return ORACLE_OK;
 }
 
-/* The whole path for one stereo pair, stage after stage.  Every stage output
- * pointer except disp may be NULL. */
+/* The whole path for one stereo pair, stage after stage.  cost_kind selects
+ * the matching cost: 0 = census Hamming distance over a cw x ch window,
+ * 1 = SAD over a cw x ch window (the codes outputs are then left untouched).
+ * Every stage output pointer except disp may be NULL. */
 int oracle_sgm(const uint8_t *left, const uint8_t *right, int W, int H,
-               int pitch, int D, int cw, int ch, int path_mask, int P1, int P2,
+               int pitch, int D, int cw, int ch, int cost_kind, int path_mask, int P1, int P2,
                int lr_tol, int median_k, uint64_t *codes_l, uint64_t *codes_r,
                uint16_t *S_out, uint8_t *DL_out, uint8_t *DR_out,
                uint8_t *lr_out, uint8_t *disp, uint16_t *U, uint16_t *V)
 {
     if (W < 1 || H < 1 || D < 1 || D > 255 || !disp) return ORACLE_EINVAL;
+    if (cost_kind != 0 && cost_kind != 1) return ORACLE_EINVAL;
     size_t npx = (size_t)W * H, nde = npx * D;
     int nbits = oracle_census_bits(cw, ch);
     uint64_t *cl = (uint64_t *)malloc(npx * sizeof(uint64_t));
     uint64_t *cr = (uint64_t *)malloc(npx * sizeof(uint64_t));
-    uint8_t *C = (uint8_t *)malloc(nde);
+    uint16_t *C = (uint16_t *)malloc(nde * sizeof(uint16_t));
     uint16_t *S = (uint16_t *)malloc(nde * sizeof(uint16_t));
     uint8_t *DL = (uint8_t *)malloc(npx), *DR = (uint8_t *)malloc(npx);
     uint8_t *lr = (uint8_t *)malloc(npx);
     int rc = ORACLE_ENOMEM;
     if (!cl || !cr || !C || !S || !DL || !DR || !lr) goto done;
-    rc = oracle_census(left, W, H, pitch, cw, ch, cl);
-    if (rc == ORACLE_OK) rc = oracle_census(right, W, H, pitch, cw, ch, cr);
-    if (rc == ORACLE_OK) rc = oracle_cost_volume(cl, cr, W, H, D, nbits, C);
+    if (cost_kind == 0) {
+        rc = oracle_census(left, W, H, pitch, cw, ch, cl);
+        if (rc == ORACLE_OK) rc = oracle_census(right, W, H, pitch, cw, ch, cr);
+        if (rc == ORACLE_OK) rc = oracle_cost_volume(cl, cr, W, H, D, nbits, C);
+    } else {
+        rc = oracle_sad_cost_volume(left, right, W, H, pitch, D, cw, ch, C);
+    }
     if (rc == ORACLE_OK) rc = oracle_sum_paths(C, W, H, D, path_mask, P1, P2, S);
     if (rc == ORACLE_OK) rc = oracle_wta_left(S, W, H, D, DL);
     if (rc == ORACLE_OK) rc = oracle_wta_right(S, W, H, D, DR);
@@ -342,8 +386,8 @@ int oracle_sgm(const uint8_t *left, const uint8_t *right, int W, int H,
     if (rc == ORACLE_OK) rc = oracle_median(lr, W, H, median_k, disp);
     if (rc == ORACLE_OK && U && V) rc = oracle_uvmap(disp, W, H, D, U, V);
     if (rc == ORACLE_OK) {
-        if (codes_l) memcpy(codes_l, cl, npx * sizeof(uint64_t));
-        if (codes_r) memcpy(codes_r, cr, npx * sizeof(uint64_t));
+        if (codes_l && cost_kind == 0) memcpy(codes_l, cl, npx * sizeof(uint64_t));
+        if (codes_r && cost_kind == 0) memcpy(codes_r, cr, npx * sizeof(uint64_t));
         if (S_out) memcpy(S_out, S, nde * sizeof(uint16_t));
         if (DL_out) memcpy(DL_out, DL, npx);
         if (DR_out) memcpy(DR_out, DR, npx);
@@ -360,7 +404,7 @@ done:
     return rc;
 }
 
-/* U-/V-map post-processing of Sec. 3.2, reading R9.  map is rows x cols
+/* U-/V-map post-processing of Sec. 3.2, reading R11.  map is rows x cols
  * uint16 (row-major); out is rows x cols uint8.  Threshold, region of
  * interest, dilation, Gaussian, in that order. */
 int oracle_uv_post(const uint16_t *map, int rows, int cols, int threshold, int r0, int r1,
@@ -407,7 +451,7 @@ int oracle_uv_post(const uint16_t *map, int rows, int cols, int threshold, int r
 }
 
 /* Rectification, Sec. 3.1.1: I_rect(x, y) = I(M_x(x, y), M_y(x, y)) with
- * integer maps of the rectified image's size (reading R10). */
+ * integer maps of the rectified image's size (reading R12). */
 int oracle_rectify(const uint8_t *img, int W, int H, int pitch, const uint16_t *mx,
                    const uint16_t *my, uint8_t *out)
 {

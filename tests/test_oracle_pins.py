@@ -395,3 +395,86 @@ def test_rectify_undoes_a_known_distortion():
     raw[ys[ok], xs[ok]] = s.right[ok]
     back = oracle.rectify(raw, np.minimum(x + shear, 0xFFFF), y + 3)
     assert np.array_equal(back[: H - 3, : W - 2], s.right[: H - 3, : W - 2])
+
+
+# --------------------------------------------------------------------------
+# SAD matching cost (Sec. 3.1.2, 5 x 5 support of Sec. 4.1; reading R13)
+# --------------------------------------------------------------------------
+
+def _sad_by_padded_box_filter(left, right, D, ww, wh):
+    """Independent construction: edge-pad both images (the clamped reads),
+    form |L - R shifted by d| on the padded grid and box-filter it with a
+    library 2-D convolution; x < d takes the maximum cost."""
+    signal = pytest.importorskip("scipy.signal")
+    H, W = left.shape
+    rw, rh = ww // 2, wh // 2
+    Lp = np.pad(left.astype(np.int64), ((rh, rh), (rw, rw)), mode="edge")
+    Rp = np.pad(right.astype(np.int64), ((rh, rh), (rw, rw)), mode="edge")
+    out = np.full((H, W, D), ww * wh * 255, np.int64)
+    for d in range(min(D, W)):
+        A = np.abs(Lp[:, d:] - Rp[:, : Rp.shape[1] - d])  # padded columns j >= d
+        out[:, d:, d] = signal.convolve2d(A, np.ones((wh, ww), np.int64), mode="valid")
+    return out
+
+
+@pytest.mark.parametrize("W,H,D,ww,wh", [(13, 9, 6, 5, 5), (21, 7, 9, 3, 5), (8, 11, 12, 1, 1),
+                                         (30, 12, 16, 7, 3)])
+def test_sad_cost_matches_padded_box_filter(W, H, D, ww, wh):
+    r = rng(90 + W)
+    left = r.integers(0, 256, (H, W)).astype(np.uint8)
+    right = r.integers(0, 256, (H, W)).astype(np.uint8)
+    got = oracle.sad_cost_volume(left, right, D, ww, wh)
+    assert np.array_equal(got, _sad_by_padded_box_filter(left, right, D, ww, wh))
+
+
+def test_sad_cost_special_cases():
+    r = rng(91)
+    img = r.integers(0, 256, (10, 17)).astype(np.uint8)
+    C = oracle.sad_cost_volume(img, img, 5, 5, 5)
+    assert (C[:, :, 0] == 0).all()                      # identical images at d = 0
+    for d in range(5):
+        assert (C[:, :d, d] == 25 * 255).all()          # x - d < 0: the maximum
+    flat = np.full((6, 9), 77, np.uint8)
+    C = oracle.sad_cost_volume(flat, flat, 4, 5, 5)
+    for d in range(4):
+        assert (C[:, d:, d] == 0).all()                 # constant images: 0 wherever x >= d
+    # a brightness offset of k adds exactly 25 k to every in-range cost
+    C = oracle.sad_cost_volume(flat + 3, flat, 4, 5, 5)
+    for d in range(4):
+        assert (C[:, d:, d] == 75).all()
+
+
+def test_sad_constant_shift_recovers_disparity():
+    d = 7
+    s = scenes.shifted_pair(72, 36, d, seed=92)
+    out = oracle.sgm(s.left, s.right, 16, 5, 5, oracle.PATHS_STREAM4, 200, 800, 1, 5,
+                     stages=True, cost=oracle.COST_SAD)
+    assert (out["disp"][3:-3, d + 3:-3] == d).all()
+    assert "codes_l" not in out
+
+
+def test_sad_stage_chain_is_consistent():
+    s = scenes.boxes_scene(40, 24, 12, seed=93, n_boxes=2, dlo=2, dhi=10)
+    o = oracle.sgm(s.left, s.right, 12, 5, 5, oracle.PATHS_8, 200, 800, 1, 3, stages=True,
+                   cost=oracle.COST_SAD)
+    C = oracle.sad_cost_volume(s.left, s.right, 12, 5, 5)
+    S = sum(oracle.aggregate_path(C, r, 200, 800).astype(np.int64) for r in range(8))
+    assert S.max() < 65536
+    assert np.array_equal(S, o["S"])
+    assert np.array_equal(np.argmin(S, axis=2), o["DL"])
+    assert np.array_equal(oracle.median(o["lr"], 3), o["disp"])
+
+
+@pytest.mark.parametrize("r", [0, 3, 4, 7])
+def test_aggregation_exhaustive_with_sad_range_costs(r):
+    """16-bit costs of the SAD range with the paper's SAD penalties (200, 800)."""
+    W, H, D, P1, P2 = 4, 3, 3, 200, 800
+    C = rng(110 + r).integers(0, 25 * 255 + 1, (H, W, D)).astype(np.uint16)
+    L = oracle.aggregate_path(C, r, P1, P2)
+    dx, dy = oracle.DIRECTIONS[r]
+    for y in range(H):
+        for x in range(W):
+            seq = _path_pixels(x, y, dx, dy, W, H)
+            bf = _brute_min_energy(C, seq, D, P1, P2)
+            off = min(_brute_min_energy(C, seq[:-1], D, P1, P2)) if len(seq) > 1 else 0
+            assert [b - off for b in bf] == L[y, x].tolist(), (x, y)

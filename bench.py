@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 from paper_1807_06271_gb300 import scenes  # noqa: E402
 
 WORKLOAD_INDEX = {"pair-320x240-d64-census5x5-4path": 0, "kitti-1242x375-d128-census9x7-8path": 1,
-                  "hd-1280x720-d128-census5x5-4path-uv": 2, "paper-640x360-d60-census5x5-stream4": 5}
+                  "hd-1280x720-d128-census5x5-4path-uv": 2, "paper-640x360-d60-census5x5-stream4": 5,
+                  "paper-640x360-d60-sad5x5-stream4": 6}
 FLUSH_BYTES = 256 << 20
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
@@ -72,11 +73,16 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 def workload_ops(w) -> dict:
     """Algorithmic integer operations per disparity estimate for the
     aggregation kernel: per enabled path 3 min + 2 add + 1 sub + 1 running
-    min = 7; the Hamming cost once per estimate: XOR + POPC for codes of up to
-    32 bits (2), two of each plus an add for 64-bit codes (5)."""
+    min = 7; the matching cost once per estimate: for the census cost XOR +
+    POPC for codes of up to 32 bits (2), two of each plus an add for 64-bit
+    codes (5); for the SAD cost, separable, an absolute difference and an add
+    per window row plus an add per window column (2 wh + ww)."""
     npaths = bin(w.path_mask).count("1")
     nbits = w.census_w * w.census_h - 1
-    cost = 2 if nbits <= 32 else 5
+    if w.cost == 1:
+        cost = 2 * w.census_h + w.census_w
+    else:
+        cost = 2 if nbits <= 32 else 5
     return {"per_path": 7, "paths": npaths, "cost": cost, "per_de": 7 * npaths + cost}
 
 
@@ -183,7 +189,7 @@ def time_oracle(w, scene, rows, reps):
     t0 = time.perf_counter()
     for _ in range(reps):
         oracle.sgm(left, right, w.D, w.census_w, w.census_h, w.path_mask, w.P1, w.P2, w.lr_tol,
-                   w.median_k, uv=w.uv)
+                   w.median_k, uv=w.uv, cost=w.cost)
     dt = time.perf_counter() - t0
     return dt, w.W * rows * w.D * reps
 
@@ -238,7 +244,8 @@ def run_ours(args, w, windex):
 
     scene = scenes.scene_for(w, rank_seed(windex, rank))
     params = sgm.SgmParams(census_w=w.census_w, census_h=w.census_h, path_mask=w.path_mask,
-                           P1=w.P1, P2=w.P2, lr_tolerance=w.lr_tol, median_k=w.median_k)
+                           P1=w.P1, P2=w.P2, lr_tolerance=w.lr_tol, median_k=w.median_k,
+                           cost=w.cost)
     h = sgm.Handle(w.W, w.H, w.D, params)
     stream = torch.cuda.current_stream()
     left = torch.from_numpy(scene.left).cuda()
@@ -375,6 +382,7 @@ def run_ours(args, w, windex):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
             "config": {"workload": w.name, "W": w.W, "H": w.H, "D": w.D,
+                       "cost": "sad" if w.cost == 1 else "census",
                        "census": f"{w.census_w}x{w.census_h}", "path_mask": w.path_mask,
                        "P1": w.P1, "P2": w.P2, "lr_tol": w.lr_tol, "median_k": w.median_k,
                        "uv_maps": w.uv, "parallelism": f"replicas{world}",

@@ -53,17 +53,32 @@ extern "C" {
 #define SGM_PATHS_STREAM4 0x55 /* 0, 45, 90, 135 degrees: the paper's streaming set
                                   (Sec. 3.1.3, Fig. 2 and Fig. 3b)                   */
 
+/* Matching costs (Sec. 3.1.2).  Both use the census_w x census_h window of
+ * sgm_params as their support region (5x5 in Sec. 4.1). */
+#define SGM_COST_CENSUS 0 /* Hamming distance of census codes: bit 1 iff the
+                             neighbour is darker than the centre, raster order,
+                             centre skipped, neighbours outside the image 0     */
+#define SGM_COST_SAD 1    /* sum of absolute differences over the window, both
+                             images read with clamped (replicated) coordinates;
+                             the paper pairs it with P1 = 200, P2 = 800         */
+
 typedef struct sgm_handle_s *sgm_handle;
 
 typedef struct sgm_params {
-    int census_w, census_h; /* census window, odd, census_w*census_h-1 <= 64 bits
-                               (Sec. 3.1.2; 5x5 in Sec. 4.1)                         */
+    int census_w, census_h; /* support window of the matching cost, both odd
+                               (Sec. 3.1.2; 5x5 in Sec. 4.1).  Census:
+                               census_w*census_h-1 <= 64 bits                   */
     int path_mask;          /* SGM_PATHS_* or any non-empty subset of 0xFF          */
-    int P1, P2;             /* penalties of Eq. 2, 0 <= P1 <= P2,
-                               census bits + P2 <= 255                              */
+    int P1, P2;             /* penalties of Eq. 2, 0 <= P1 <= P2.  Census:
+                               bits + P2 <= 255 (8-bit path costs).  SAD
+                               (window sides <= 15): with cmax =
+                               census_w*census_h*255, cmax + P2 <= 32766 and
+                               (cmax + P2) * (number of paths) <= 65535
+                               (16-bit path costs whose sum fits 16 bits)     */
     int lr_tolerance;       /* Sec. 3.1.4; < 0 switches the check off                */
     int median_k;           /* Sec. 3.1.5; 0 or 1 = off, else odd, <= 7             */
     int row_pitch;          /* bytes between image rows; 0 = W                       */
+    int cost;               /* SGM_COST_CENSUS (0, the default) or SGM_COST_SAD      */
 } sgm_params;
 
 /* Create a handle for W x H images and D disparities (1 <= D <= 255) and
@@ -76,7 +91,7 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out);
 int sgm_destroy(sgm_handle h);
 
 /* Dense disparity of one rectified pair (Sec. 3.1): census transform and
- * Hamming cost (Sec. 3.1.2, Eq. 1), aggregation along the enabled paths with
+ * Hamming cost, or SAD (Sec. 3.1.2, Eq. 1), aggregation along the enabled paths with
  * P1/P2 (Sec. 3.1.3, Eq. 2), winner-takes-all, right disparity from the same
  * aggregated volume and left-right check (Sec. 3.1.4), k x k median
  * (Sec. 3.1.5).  left/right: device, H rows of row_pitch bytes.  disp: device,
@@ -160,14 +175,15 @@ int sgm_set_rectification(sgm_handle h, const uint16_t *left_x, const uint16_t *
 
 /* ---- per-stage parity access (same kernels as sgm_compute) --------------- */
 
-/* Census codes (Sec. 3.1.2), one uint64 per pixel, H x W each (device). */
+/* Census codes (Sec. 3.1.2), one uint64 per pixel, H x W each (device).
+ * SGM_ERR_UNSUPPORTED for a handle with the SAD cost (it has no codes). */
 int sgm_debug_census(sgm_handle h, const uint8_t *left, const uint8_t *right,
                      uint64_t *codes_left, uint64_t *codes_right, void *stream);
 
-/* Aggregated cost L_r of direction r alone (Eq. 2), H x W x D bytes (device),
- * d fastest.  r must be enabled in the handle's path mask. */
+/* Aggregated cost L_r of direction r alone (Eq. 2), H x W x D uint16
+ * (device), d fastest.  r must be enabled in the handle's path mask. */
 int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *right,
-                   uint8_t *L, void *stream);
+                   uint16_t *L, void *stream);
 
 /* Sum over the enabled paths S = C_aggr (Sec. 3.1.3), H x W x D uint16 (device). */
 int sgm_debug_sum(sgm_handle h, const uint8_t *left, const uint8_t *right,
@@ -209,9 +225,10 @@ const char *sgm_stage_name(int i);
  *   Arguments and checks as sgm_create + sgm_compute: left/right are device
  *   images of H rows of row_pitch bytes, disp is a device H x W byte map.
  *   Scratch: census codes (2*W*H*4 bytes when census_w*census_h-1 <= 32, else
- *   2*W*H*8), a cost volume and one plane per enabled path of W*H*Dp bytes
- *   each (Dp = D rounded up to 8 times a power of two: 8, 16, 32, 64, 128 or
- *   256), a 256-byte work counter and a W*H byte map, each rounded up to 256
+ *   2*W*H*8; none for SGM_COST_SAD), a cost volume and one plane per enabled
+ *   path of W*H*Dp*e bytes each (Dp = D rounded up to 8 times a power of two:
+ *   8, 16, 32, 64, 128 or 256; e = 1 for census, 2 for SAD), the aggregation's
+ *   work-queue state (4224 bytes) and a W*H byte map, each rounded up to 256
  *   bytes.  A call that needs more than SGM_STATIC_SCRATCH_BYTES returns
  *   SGM_ERR_UNSUPPORTED before any GPU work (320x240 with D=64 and 4 paths
  *   needs about 25 MiB).

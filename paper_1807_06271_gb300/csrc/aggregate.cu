@@ -42,11 +42,15 @@
 // cost loads that bypass L1 (L1::no_allocate: 12 % slower, .cg: 6 %).
 //
 // Memory.  The cost of step t + PF is loaded while step t computes (a ring of
-// PF = 16 DPL-byte registers).  While every scanline of the warp has at
-// least 2 * PF steps left the loop runs without bounds checks.  Each step
-// stores the lane's DPL path costs to the direction's plane, in the cost
-// volume's byte order, with evict_first: the planes are read back only once,
-// by the WTA kernel.
+// PF lane chunks: 16 of 8 bytes for 8-bit costs, 8 of 16 bytes for the
+// 16-bit costs of SAD).  While every scanline of the warp has at least 2 * PF
+// steps left the loop runs without bounds checks.  Each step stores the
+// lane's DPL path costs to the direction's plane, in the cost volume's order
+// and width, with evict_first: the planes are read back only once, by the
+// WTA kernel.  16-bit path costs run through the same packed arithmetic: the
+// host keeps cmax + P2 below the 0x7FFF padding marker.
+#include <type_traits>
+
 #include "sgm_internal.cuh"
 
 namespace sgm {
@@ -127,28 +131,30 @@ __device__ __forceinline__ unsigned next_job(unsigned *state, unsigned nlong, un
     return jl < nlong ? jl : total;
 }
 
-// Chunk of DPL bytes: 8 -> uint2, 16 -> uint4.
-template <int DPL>
-struct Chunk;
-template <>
-struct Chunk<8> {
-    using T = uint2;
-    static __device__ __forceinline__ T zero() { return make_uint2(0u, 0u); }
-    static __device__ __forceinline__ uint32_t word(const T &c, int w) { return w == 0 ? c.x : c.y; }
-};
-template <>
-struct Chunk<16> {
-    using T = uint4;
-    static __device__ __forceinline__ T zero() { return make_uint4(0u, 0u, 0u, 0u); }
-    static __device__ __forceinline__ uint32_t word(const T &c, int w) {
-        return w == 0 ? c.x : w == 1 ? c.y : w == 2 ? c.z : c.w;
-    }
+// One lane's chunk of DPL disparities in memory: DPL bytes (8-bit costs) or
+// 2*DPL bytes (16-bit, "wide"), as uint2 or uint4.
+template <int DPL, bool WIDE>
+struct Lane {
+    static constexpr int kBytes = WIDE ? 2 * DPL : DPL;
+    static_assert(kBytes == 8 || kBytes == 16, "a lane chunk is 8 or 16 bytes");
+    using T = typename std::conditional<kBytes == 8, uint2, uint4>::type;
+    static constexpr int kWords = kBytes / 4;
 };
 
-template <int DPL>
-__device__ __forceinline__ typename Chunk<DPL>::T ld_chunk(const typename Chunk<DPL>::T *p) {
-    typename Chunk<DPL>::T v;
-    if constexpr (DPL == 8) {
+__device__ __forceinline__ uint32_t word_of(const uint2 &c, int w) { return w == 0 ? c.x : c.y; }
+__device__ __forceinline__ uint32_t word_of(const uint4 &c, int w) {
+    return w == 0 ? c.x : w == 1 ? c.y : w == 2 ? c.z : c.w;
+}
+template <typename T>
+__device__ __forceinline__ T chunk_of(const uint32_t *w) {
+    if constexpr (sizeof(T) == 8) return make_uint2(w[0], w[1]);
+    else return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_chunk(const T *p) {
+    T v;
+    if constexpr (sizeof(T) == 8) {
         asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     } else {
         asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -157,10 +163,9 @@ __device__ __forceinline__ typename Chunk<DPL>::T ld_chunk(const typename Chunk<
     }
     return v;
 }
-template <int DPL>
-__device__ __forceinline__ void st_chunk(typename Chunk<DPL>::T *p, const typename Chunk<DPL>::T &v,
-                                         uint64_t pol) {
-    if constexpr (DPL == 8) {
+template <typename T>
+__device__ __forceinline__ void st_chunk(T *p, const T &v, uint64_t pol) {
+    if constexpr (sizeof(T) == 8) {
         asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p),
                      "r"(v.x), "r"(v.y), "l"(pol)
                      : "memory");
@@ -169,6 +174,11 @@ __device__ __forceinline__ void st_chunk(typename Chunk<DPL>::T *p, const typena
                      "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
                      : "memory");
     }
+}
+template <typename T>
+__device__ __forceinline__ T zero_chunk() {
+    const uint32_t z[4] = {0u, 0u, 0u, 0u};
+    return chunk_of<T>(z);
 }
 
 // (m, m) with m the minimum over the LPS lanes of this lane's scanline of
@@ -212,17 +222,22 @@ struct PathState {
 };
 
 // One step of Eq. 2 for the lane's DPL disparities with cost chunk c.
-template <int LPS, int DPL, bool RAGGED>
-__device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Chunk<DPL>::T &c,
+template <int LPS, int DPL, bool WIDE, bool RAGGED>
+__device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Lane<DPL, WIDE>::T &c,
                                           uint32_t P1x2, uint32_t P2x2, int grp, uint32_t lo_edge,
                                           uint32_t hi_edge, const uint32_t (&inv)[DPL / 2]) {
     constexpr int NR = DPL / 2;
     uint32_t cc[NR];
+    if constexpr (WIDE) {
 #pragma unroll
-    for (int w = 0; w < DPL / 4; w++) {
-        const uint32_t v = Chunk<DPL>::word(c, w);
-        cc[2 * w] = v & kLo;                         // bytes 0, 2
-        cc[2 * w + 1] = __byte_perm(v, 0u, 0x4341);  // bytes 1, 3
+        for (int k = 0; k < NR; k++) cc[k] = word_of(c, k);  // (C[k], C[k+h]) as stored
+    } else {
+#pragma unroll
+        for (int w = 0; w < DPL / 4; w++) {
+            const uint32_t v = word_of(c, w);
+            cc[2 * w] = v & kLo;                         // bytes 0, 2
+            cc[2 * w + 1] = __byte_perm(v, 0u, 0x4341);  // bytes 1, 3
+        }
     }
     const uint32_t prev = __shfl_up_sync(0xffffffffu, st.R[NR - 1], 1);
     const uint32_t next = __shfl_down_sync(0xffffffffu, st.R[0], 1);
@@ -248,30 +263,38 @@ __device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Chu
     st.mP2 = st.m2 + P2x2;
 }
 
-// The lane's DPL path costs as the plane's bytes (cost-volume byte order).
-template <int DPL, bool RAGGED>
-__device__ __forceinline__ typename Chunk<DPL>::T pack_plane(const PathState<DPL> &st) {
-    uint32_t w[DPL / 4];
+// The lane's DPL path costs in the cost volume's order.  Padding slots
+// (0x7FFF) are stored as their low byte (8-bit) or as 0 (16-bit), so that sums
+// over the planes never carry out of a 16-bit half; no WTA key uses them.
+template <int DPL, bool WIDE, bool RAGGED>
+__device__ __forceinline__ typename Lane<DPL, WIDE>::T pack_plane(const PathState<DPL> &st,
+                                                                  const uint32_t (&inv)[DPL / 2]) {
+    using CT = typename Lane<DPL, WIDE>::T;
+    uint32_t w[Lane<DPL, WIDE>::kWords];
+    if constexpr (WIDE) {
 #pragma unroll
-    for (int i = 0; i < DPL / 4; i++) {
-        uint32_t a = st.R[2 * i], b = st.R[2 * i + 1];
-        if (RAGGED) {
-            a &= kLo;
-            b &= kLo;
+        for (int k = 0; k < DPL / 2; k++) w[k] = RAGGED ? st.R[k] & ~inv[k] : st.R[k];
+    } else {
+#pragma unroll
+        for (int i = 0; i < DPL / 4; i++) {
+            uint32_t a = st.R[2 * i], b = st.R[2 * i + 1];
+            if (RAGGED) {
+                a &= kLo;
+                b &= kLo;
+            }
+            w[i] = b * 256u + a;
         }
-        w[i] = b * 256u + a;
     }
-    if constexpr (DPL == 8) return make_uint2(w[0], w[1]);
-    else return make_uint4(w[0], w[1], w[2], w[3]);
+    return chunk_of<CT>(w);
 }
 
-template <int LPS, int DPL, bool RAGGED, int PF>
+template <int LPS, int DPL, bool WIDE, bool RAGGED, int PF>
 __global__ void __launch_bounds__(kWarps * 32)
-    aggregate_kernel(const typename Chunk<DPL>::T *__restrict__ cost, int W, int H, int D,
+    aggregate_kernel(const typename Lane<DPL, WIDE>::T *__restrict__ cost, int W, int H, int D,
                      uint32_t P1x2, uint32_t P2x2, PathJobs jobs,
-                     typename Chunk<DPL>::T *__restrict__ planes, int nplanes,
+                     typename Lane<DPL, WIDE>::T *__restrict__ planes, int nplanes,
                      unsigned *__restrict__ job_counter) {
-    using CT = typename Chunk<DPL>::T;
+    using CT = typename Lane<DPL, WIDE>::T;
     constexpr int G = 32 / LPS, NR = DPL / 2;
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPS, li = lane % LPS;
@@ -330,7 +353,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         CT ring[PF];
 #pragma unroll
         for (int i = 0; i < PF; i++) {
-            ring[i] = i < len ? ld_chunk<DPL>(cost + ci_ld) : Chunk<DPL>::zero();
+            ring[i] = i < len ? ld_chunk(cost + ci_ld) : zero_chunk<CT>();
             ci_ld += cstep;
         }
         PathState<DPL> st;
@@ -347,10 +370,10 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
             for (int i = 0; i < PF; i++) {
                 const CT c = ring[i];
-                ring[i] = ld_chunk<DPL>(cost + ci_ld);
+                ring[i] = ld_chunk(cost + ci_ld);
                 ci_ld += cstep;
-                path_step<LPS, DPL, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
+                path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+                st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
                 oi += ostep;
             }
             rem -= PF;
@@ -359,10 +382,10 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
             for (int i = 0; i < PF; i++) {
                 const CT c = ring[i];
-                if (rem > PF) ring[i] = ld_chunk<DPL>(cost + ci_ld);
+                if (rem > PF) ring[i] = ld_chunk(cost + ci_ld);
                 ci_ld += cstep;
-                path_step<LPS, DPL, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                if (rem > 0) st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
+                path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+                if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
                 oi += ostep;
                 rem--;
             }
@@ -370,8 +393,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
         for (int i = 0; i < PF; i++) {  // the last steps < PF
             if (t0 + i < steps) {
-                path_step<LPS, DPL, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                if (rem > 0) st_chunk<DPL>(planes + oi, pack_plane<DPL, RAGGED>(st), pol_stream);
+                path_step<LPS, DPL, WIDE, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+                if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
                 oi += ostep;
                 rem--;
             }
@@ -379,38 +402,62 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 }
 
-template <int LPS, int DPL>
+template <int LPS, int DPL, bool WIDE>
 cudaError_t launch_lps(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                        const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
                        int blocks, cudaStream_t s) {
-    using CT = typename Chunk<DPL>::T;
-    constexpr int PF = 16;  // cost loads issued PF steps ahead
+    using CT = typename Lane<DPL, WIDE>::T;
+    // cost loads issued PF steps ahead: 16 chunks of 8 bytes, 8 of 16 bytes
+    constexpr int PF = sizeof(CT) == 8 ? 16 : 8;
     const CT *c = reinterpret_cast<const CT *>(cost);
     CT *p = reinterpret_cast<CT *>(planes);
     if (D == DPL * LPS)
-        aggregate_kernel<LPS, DPL, false, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
+        aggregate_kernel<LPS, DPL, WIDE, false, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
     else
-        aggregate_kernel<LPS, DPL, true, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
+        aggregate_kernel<LPS, DPL, WIDE, true, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
     return cudaGetLastError();
 }
 
-// Plane 0 ([H][W][Dp], lane-chunk byte order) -> L ([H][W][D], natural order).
+template <bool WIDE>
+cudaError_t launch_all(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
+                       const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
+                       int blocks, cudaStream_t s) {
+#define SGM_AGG(L) launch_lps<L, 8, WIDE>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s)
+    switch (lanes_per_scanline(D)) {
+        case 1: return SGM_AGG(1);
+        case 2: return SGM_AGG(2);
+        case 4: return SGM_AGG(4);
+        case 8: return SGM_AGG(8);
+        case 16: return SGM_AGG(16);
+        default: return SGM_AGG(32);
+    }
+#undef SGM_AGG
+}
+
+// Plane 0 ([H][W][Dp], lane-chunk order) -> L ([H][W][D] uint16, natural order).
 __global__ void unpermute_kernel(const uint8_t *__restrict__ plane, int npx, int D, int Dp, int dpl,
-                                 uint8_t *__restrict__ L) {
+                                 bool wide, uint16_t *__restrict__ L) {
     const size_t n = (size_t)npx * D;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t p = i / D;
-        const int d = (int)(i - p * D);
-        L[i] = plane[p * Dp + dpl * (d / dpl) + chunk_byte(dpl, d % dpl)];
+        const int d = (int)(i - p * D), j = d % dpl;
+        if (wide) {
+            // word k of a chunk holds the pair (k, k + dpl/2) as two uint16
+            const uint16_t *w = reinterpret_cast<const uint16_t *>(plane);
+            L[i] = w[p * Dp + dpl * (d / dpl) + 2 * (j % (dpl / 2)) + j / (dpl / 2)];
+        } else {
+            L[i] = plane[p * Dp + dpl * (d / dpl) + chunk_byte(dpl, j)];
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2,
+cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2, bool wide,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
                              unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
     if (jobs.jbegin[jobs.n] == 0) return cudaSuccess;
+    if (disparities_per_lane(D) != 8) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(job_counter, 0, kJobStateBytes, s);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -419,24 +466,18 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
     if (e != cudaSuccess) return e;
     const int blocks = sms * (blocks_per_sm > 0 ? blocks_per_sm : 2);
     const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
-#define SGM_AGG(L, P) launch_lps<L, P>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s)
-    switch (lanes_per_scanline(D)) {
-        case 1: return SGM_AGG(1, 8);
-        case 2: return SGM_AGG(2, 8);
-        case 4: return SGM_AGG(4, 8);
-        case 8: return SGM_AGG(8, 8);
-        case 16: return SGM_AGG(16, 8);
-        default: return SGM_AGG(32, 8);
-    }
-#undef SGM_AGG
+    if (wide) return launch_all<true>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+    return launch_all<false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
 }
 
-cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, uint8_t *L, cudaStream_t s) {
+cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,
+                             cudaStream_t s) {
     const int npx = W * H;
     const size_t n = (size_t)npx * D;
     const size_t want = (n + 255) / 256;
     const int blocks = (int)(want < 4096 ? want : 4096);
-    unpermute_kernel<<<blocks, 256, 0, s>>>(plane, npx, D, padded_disparities(D), disparities_per_lane(D), L);
+    unpermute_kernel<<<blocks, 256, 0, s>>>(plane, npx, D, padded_disparities(D), disparities_per_lane(D),
+                                            wide, L);
     return cudaGetLastError();
 }
 

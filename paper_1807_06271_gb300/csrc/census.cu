@@ -24,20 +24,6 @@ constexpr int kRows = 4;  // rows per thread of the unrolled census kernel
 // the image": 255 is never darker than a centre pixel, which gives the 0 bit
 // the border rule asks for.  Each bit is the sign of I(q) - I(p), shifted
 // into one of two 32-bit halves (two instructions per bit).
-// Pixel (gx, gy) of the rectified image: the source image read through the
-// maps (Sec. 3.1.1), 0 where a map entry leaves the source.
-template <bool RECT>
-__device__ __forceinline__ uint8_t rect_pixel(const uint8_t *__restrict__ img, int pitch, int W,
-                                              int H, int gx, int gy, const uint16_t *__restrict__ mx,
-                                              const uint16_t *__restrict__ my) {
-    if constexpr (!RECT) {
-        return img[(size_t)gy * pitch + gx];
-    } else {
-        const int sx = mx[(size_t)gy * W + gx], sy = my[(size_t)gy * W + gx];
-        return (sx < W && sy < H) ? img[(size_t)sy * pitch + sx] : 0;
-    }
-}
-
 template <typename CodeT, int CW, int CH, bool RECT>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,

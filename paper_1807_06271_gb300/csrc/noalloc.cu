@@ -53,8 +53,10 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     if (!left || !right || !disp) return SGM_ERR_INVALID_ARG;
     int rc = sgm::validate_params(W, H, D, params);
     if (rc != SGM_OK) return rc;
+    const bool wide = params->cost == SGM_COST_SAD;
     const int nbits = params->census_w * params->census_h - 1;
-    const int code_bytes = nbits <= 32 ? 4 : 8;
+    const int code_bytes = wide ? 0 : (nbits <= 32 ? 4 : 8);
+    const size_t eb = wide ? 2 : 1;  // bytes per cost / path cost
     const int npaths = __builtin_popcount((unsigned)params->path_mask);
     const int Dp = sgm::padded_disparities(D);
 
@@ -63,8 +65,8 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     const size_t npx = (size_t)W * H;
     const size_t codes_off = 0;
     const size_t cost_off = round_up(codes_off + 2 * npx * code_bytes, 256);
-    const size_t planes_off = round_up(cost_off + npx * Dp, 256);
-    const size_t counter_off = round_up(planes_off + (size_t)npaths * npx * Dp, 256);
+    const size_t planes_off = round_up(cost_off + npx * Dp * eb, 256);
+    const size_t counter_off = round_up(planes_off + (size_t)npaths * npx * Dp * eb, 256);
     const size_t lr_off = round_up(counter_off + sgm::kJobStateBytes, 256);
     const size_t need = lr_off + npx;
     if (need > (size_t)SGM_STATIC_SCRATCH_BYTES) return SGM_ERR_UNSUPPORTED;
@@ -84,14 +86,21 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     // nothing left by an earlier call needs clearing.
     cudaStream_t s = (cudaStream_t)stream;
     const int pitch = params->row_pitch ? params->row_pitch : W;
-    cudaError_t e = sgm::launch_census(left, right, pitch, W, H, params->census_w, params->census_h,
-                                       code_bytes, codes, sgm::RectMaps{nullptr, nullptr, nullptr, nullptr}, s);
-    if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, s);
+    const sgm::RectMaps no_maps{nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e;
+    if (wide) {
+        e = sgm::launch_sad_cost(left, right, pitch, W, H, D, params->census_w, params->census_h, no_maps,
+                                 reinterpret_cast<uint16_t *>(cost), s);
+    } else {
+        e = sgm::launch_census(left, right, pitch, W, H, params->census_w, params->census_h, code_bytes,
+                               codes, no_maps, s);
+        if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, s);
+    }
     if (e == cudaSuccess)
-        e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, jobs, planes, npaths,
+        e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, wide, jobs, planes, npaths,
                                   counter, 2, s);
     if (e == cudaSuccess)
-        e = sgm::launch_wta(planes, npaths, W, H, D, params->lr_tolerance, disp_lr, nullptr, nullptr,
+        e = sgm::launch_wta(planes, npaths, W, H, D, wide, params->lr_tolerance, disp_lr, nullptr, nullptr,
                             nullptr, s);
     if (e == cudaSuccess) {
         if (params->median_k <= 1)

@@ -23,16 +23,25 @@ int validate(int W, int H, int D, const sgm_params *p) {
     if (p->P1 < 0 || p->P2 < p->P1) return SGM_ERR_INVALID_ARG;
     if (p->row_pitch != 0 && p->row_pitch < W) return SGM_ERR_INVALID_ARG;
     if (p->median_k < 0 || (p->median_k > 1 && !(p->median_k & 1))) return SGM_ERR_INVALID_ARG;
-    const int nbits = p->census_w * p->census_h - 1;
-    if (nbits > 64) return SGM_ERR_UNSUPPORTED;
-    if (nbits + p->P2 > 255) return SGM_ERR_UNSUPPORTED;  // L_r must fit a byte
+    if (p->cost != SGM_COST_CENSUS && p->cost != SGM_COST_SAD) return SGM_ERR_INVALID_ARG;
+    const int npaths = __builtin_popcount((unsigned)p->path_mask);
+    if (p->cost == SGM_COST_CENSUS) {
+        const int nbits = p->census_w * p->census_h - 1;
+        if (nbits > 64) return SGM_ERR_UNSUPPORTED;
+        if (nbits + p->P2 > 255) return SGM_ERR_UNSUPPORTED;  // L_r must fit a byte
+    } else {
+        if (p->census_w > kMaxSadWindow || p->census_h > kMaxSadWindow) return SGM_ERR_UNSUPPORTED;
+        // 16-bit path costs: below the 0x7FFF padding marker, and their sum over
+        // the paths within 16 bits
+        const long long top = (long long)p->census_w * p->census_h * 255 + p->P2;
+        if (top > 0x7FFE || top * npaths > 0xFFFF) return SGM_ERR_UNSUPPORTED;
+    }
     if (D > kMaxD || W > kMaxW || H > 65535) return SGM_ERR_UNSUPPORTED;
     if (p->median_k > 7) return SGM_ERR_UNSUPPORTED;
     // kernels index the per-path planes with 32-bit counts of lane chunks (one
-    // lane's disparities of one pixel); the cost prefetch runs up to 32 steps
-    // of W + 1 pixels past a scanline's end
-    const long long chunks = ((long long)W * H * __builtin_popcount((unsigned)p->path_mask) +
-                              64ll * (W + 1)) * lanes_per_scanline(D);
+    // lane's disparities of one pixel); the cost ring's index runs up to 16
+    // steps of W + 1 pixels past a scanline's end
+    const long long chunks = ((long long)W * H * npaths + 64ll * (W + 1)) * lanes_per_scanline(D);
     if (chunks >= (1ll << 31)) return SGM_ERR_UNSUPPORTED;
     return SGM_OK;
 }
@@ -88,6 +97,7 @@ void stage_end(sgm_handle_s *h, TimingRecord *rec, cudaStream_t s) {
 // ---- the pipeline -----------------------------------------------------------
 
 int run_census(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaStream_t s) {
+    if (h->wide) return SGM_ERR_UNSUPPORTED;  // the SAD cost has no census codes
     const int pitch = h->p.row_pitch ? h->p.row_pitch : h->W;
     TimingRecord *t = stage_begin(h, kStageCensus, s);
     cudaError_t e = launch_census(left, right, pitch, h->W, h->H, h->p.census_w, h->p.census_h,
@@ -96,18 +106,32 @@ int run_census(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaS
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
 
-int run_cost(sgm_handle_s *h, cudaStream_t s) {
+int run_cost(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaStream_t s) {
     TimingRecord *t = stage_begin(h, kStageCost, s);
-    cudaError_t e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, s);
+    cudaError_t e;
+    if (h->wide) {
+        const int pitch = h->p.row_pitch ? h->p.row_pitch : h->W;
+        e = launch_sad_cost(left, right, pitch, h->W, h->H, h->D, h->p.census_w, h->p.census_h, h->rect,
+                            reinterpret_cast<uint16_t *>(h->cost), s);
+    } else {
+        e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, s);
+    }
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
+// The matching-cost volume of one pair: census codes then Hamming costs, or SAD.
+int run_matching(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaStream_t s) {
+    int rc = h->wide ? SGM_OK : run_census(h, left, right, s);
+    if (rc == SGM_OK) rc = run_cost(h, left, right, s);
+    return rc;
 }
 
 // All enabled directions into h->planes, or direction only_r alone into plane 0.
 int run_aggregate(sgm_handle_s *h, int only_r, cudaStream_t s) {
     const PathJobs jobs = make_path_jobs(h->W, h->H, h->D, only_r >= 0 ? (1 << only_r) : h->p.path_mask);
     TimingRecord *t = stage_begin(h, kStageAggregate, s);
-    cudaError_t e = launch_aggregate(h->cost, h->W, h->H, h->D, h->p.P1, h->p.P2, jobs, h->planes,
+    cudaError_t e = launch_aggregate(h->cost, h->W, h->H, h->D, h->p.P1, h->p.P2, h->wide != 0, jobs, h->planes,
                                      only_r >= 0 ? 1 : h->npaths, h->job_counter, h->agg_blocks_per_sm, s);
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
@@ -116,7 +140,7 @@ int run_aggregate(sgm_handle_s *h, int only_r, cudaStream_t s) {
 int run_wta(sgm_handle_s *h, uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum,
             cudaStream_t s) {
     TimingRecord *t = stage_begin(h, kStageWta, s);
-    cudaError_t e = launch_wta(h->planes, h->npaths, h->W, h->H, h->D,
+    cudaError_t e = launch_wta(h->planes, h->npaths, h->W, h->H, h->D, h->wide != 0,
                                h->p.lr_tolerance, h->disp_lr, dbg_left, dbg_right, dbg_sum, s);
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
@@ -135,8 +159,7 @@ int run_median(sgm_handle_s *h, uint8_t *disp, cudaStream_t s) {
 
 int compute_on(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
                cudaStream_t s) {
-    int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_cost(h, s);
+    int rc = run_matching(h, left, right, s);
     if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
     if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, nullptr, s);
     if (rc == SGM_OK) rc = run_median(h, disp, s);
@@ -227,8 +250,9 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     h->H = H;
     h->D = D;
     h->p = *params;
-    h->nbits = params->census_w * params->census_h - 1;
-    h->code_bytes = h->nbits <= 32 ? 4 : 8;
+    h->wide = params->cost == SGM_COST_SAD;
+    h->nbits = h->wide ? params->census_w * params->census_h * 255 : params->census_w * params->census_h - 1;
+    h->code_bytes = h->wide ? 0 : (h->nbits <= 32 ? 4 : 8);
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         free(h);
         cudaGetLastError();
@@ -245,10 +269,11 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
         if (v >= 1 && v <= 16) h->agg_blocks_per_sm = v;
     }
     const size_t npx = (size_t)W * H;
-    rc = dev_alloc(&h->codes, 2 * npx * h->code_bytes);
-    if (rc == SGM_OK) rc = dev_alloc(&h->cost, npx * h->Dp);
+    const size_t eb = h->wide ? 2 : 1;  // bytes per cost / path cost
+    rc = h->wide ? SGM_OK : dev_alloc(&h->codes, 2 * npx * h->code_bytes);
+    if (rc == SGM_OK) rc = dev_alloc(&h->cost, npx * h->Dp * eb);
     if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, kJobStateBytes);
-    if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * h->Dp);
+    if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * h->Dp * eb);
     if (rc == SGM_OK) rc = dev_alloc(&h->disp_lr, npx);
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
         rc = SGM_ERR_CUDA;
@@ -368,17 +393,16 @@ int sgm_debug_census(sgm_handle h, const uint8_t *left, const uint8_t *right, ui
     return SGM_OK;
 }
 
-int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *right, uint8_t *L,
+int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *right, uint16_t *L,
                    void *stream) {
     if (!h || !left || !right || !L || r < 0 || r >= kMaxPaths) return SGM_ERR_INVALID_ARG;
     if (!((h->p.path_mask >> r) & 1)) return SGM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_cost(h, s);
+    int rc = run_matching(h, left, right, s);
     if (rc == SGM_OK) rc = run_aggregate(h, r, s);
-    if (rc == SGM_OK && launch_unpermute(h->planes, h->W, h->H, h->D, L, s) != cudaSuccess)
+    if (rc == SGM_OK && launch_unpermute(h->planes, h->W, h->H, h->D, h->wide != 0, L, s) != cudaSuccess)
         rc = SGM_ERR_CUDA;
     return rc;
 }
@@ -388,8 +412,7 @@ int sgm_debug_sum(sgm_handle h, const uint8_t *left, const uint8_t *right, uint1
     DeviceGuard g(h->device);
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_cost(h, s);
+    int rc = run_matching(h, left, right, s);
     if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
     if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, S, s);
     return rc;
@@ -401,8 +424,7 @@ int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8
     DeviceGuard g(h->device);
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = run_census(h, left, right, s);
-    if (rc == SGM_OK) rc = run_cost(h, s);
+    int rc = run_matching(h, left, right, s);
     if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
     if (rc == SGM_OK) rc = run_wta(h, disp_left, disp_right, nullptr, s);
     if (rc == SGM_OK && disp_lr &&

@@ -11,6 +11,7 @@ namespace sgm {
 constexpr int kMaxPaths = 8;
 constexpr int kMaxD = 255;
 constexpr int kMaxW = 8192;  // the right-WTA keeps one 32-bit key per column in shared memory
+constexpr int kMaxSadWindow = 15;  // largest SAD support window side (shared-memory rows of the cost kernel)
 
 // Path directions (dx, dy), bit r of a path mask enables entry r.
 __host__ __device__ constexpr int dir_dx(int r) {
@@ -34,17 +35,34 @@ struct RectMaps {
     const uint16_t *lx, *ly, *rx, *ry;
 };
 
+// Pixel (gx, gy) of the rectified image: the source image read through the
+// maps (Sec. 3.1.1), 0 where a map entry leaves the source.
+template <bool RECT>
+__device__ __forceinline__ uint8_t rect_pixel(const uint8_t *__restrict__ img, int pitch, int W,
+                                              int H, int gx, int gy, const uint16_t *__restrict__ mx,
+                                              const uint16_t *__restrict__ my) {
+    if constexpr (!RECT) {
+        return img[(size_t)gy * pitch + gx];
+    } else {
+        const int sx = mx[(size_t)gy * W + gx], sy = my[(size_t)gy * W + gx];
+        return (sx < W && sy < H) ? img[(size_t)sy * pitch + sx] : 0;
+    }
+}
+
 // Disparity layout.  The D disparities of a pixel are held by LPS lanes
 // ("lanes per scanline", a power of two) with DPL = 8 disparities each, so a
-// pixel owns Dp = DPL * LPS bytes in the cost volume and in every path plane;
+// pixel owns Dp = DPL * LPS slots in the cost volume and in every path plane;
 // slots d >= D are padding.  A lane's chunk (disparities DPL*i .. DPL*i + DPL-1)
-// is DPL/4 32-bit words; with h = DPL/2, word w holds the bytes
-// d+2w  d+2w+1  d+2w+h  d+2w+1+h,  so masking a word with 0x00FF00FF (directly,
-// or after one byte-permute) yields the packed 16-bit pairs (d+k, d+k+h) the
-// aggregation kernel works on.  The kernels are written for any DPL that is a
-// multiple of 4; 16 per lane was measured slower on the 1242 x 375, D = 128
-// workload (fewer, fatter warps lengthen the horizontal scanlines, which set
-// the aggregation's duration), so 8 is used for every D.
+// is stored so that the aggregation kernel gets the packed 16-bit pairs
+// (d+k, d+k+h), h = DPL/2, it works on with at most one mask or byte-permute:
+//   8-bit costs (census): DPL/4 32-bit words, word w holding the bytes
+//     d+2w  d+2w+1  d+2w+h  d+2w+1+h  (mask 0x00FF00FF, or permute, per pair);
+//   16-bit costs (SAD, "wide"): DPL/2 32-bit words, word k holding the
+//     uint16 pair (d+k, d+k+h) itself.
+// The kernels are written for any DPL that is a multiple of 4; 16 per lane was
+// measured slower on the 1242 x 375, D = 128 workload (fewer, fatter warps
+// lengthen the horizontal scanlines, which set the aggregation's duration), so
+// 8 is used for every D.
 inline int disparities_per_lane(int) { return 8; }
 inline int lanes_per_scanline(int D) {
     const int dpl = disparities_per_lane(D);
@@ -91,8 +109,9 @@ struct TimingRecord {
 struct sgm_handle_s {
     int W, H, D;
     sgm_params p;
-    int nbits;       // census bits
-    int code_bytes;  // 4 (nbits <= 32) or 8
+    int nbits;       // largest matching cost: census bits, or window * 255 for SAD
+    int code_bytes;  // census: 4 (nbits <= 32) or 8; SAD: 0 (no codes)
+    int wide;        // 1: 16-bit costs and path costs (SAD), 0: 8-bit (census)
     int device;
     int npaths;
     int path_of_plane[sgm::kMaxPaths];
@@ -100,9 +119,9 @@ struct sgm_handle_s {
     int Dp;          // padded disparities per pixel (8 * lanes per scanline)
 
     // scratch, owned
-    void *codes;        // [2][H][W] census codes (left, right)
-    uint8_t *cost;      // [H][W][Dp] matching cost, lane-chunk byte order
-    uint8_t *planes;    // [H][W][npaths][Dp] per-path aggregated costs, same byte order
+    void *codes;        // [2][H][W] census codes (left, right); null for SAD
+    uint8_t *cost;      // [H][W][Dp] matching cost, lane-chunk order (bytes, or uint16 when wide)
+    uint8_t *planes;    // [H][W][npaths][Dp] per-path aggregated costs, same order
     uint8_t *disp_lr;   // [H][W] after the LR check, before the median
     unsigned *job_counter;  // work-queue state of the aggregation kernel (kJobStateBytes)
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
@@ -132,15 +151,22 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
                           cudaStream_t s);
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
                         uint8_t *cost, cudaStream_t s);
+// SAD over a ww x wh window (clamped reads; rectified through maps when set) into a
+// 16-bit cost volume [H][W][Dp] in the wide lane-chunk order.
+cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
+                            int D, int ww, int wh, const RectMaps &maps, uint16_t *cost,
+                            cudaStream_t s);
 // Planes are pixel-interleaved: [H][W][nplanes][Dp], entry k of `jobs` writing
 // plane jobs.plane[k].  job_counter (kJobStateBytes) is cleared on s before
 // the kernel starts.
-cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2,
+// wide: 16-bit costs and planes (SAD), else 8-bit.
+cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2, bool wide,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
                              unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
-// Copies a single plane ([H][W][Dp], lane-chunk order) to L ([H][W][D], natural order).
-cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, uint8_t *L, cudaStream_t s);
-cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
+// Copies a single plane ([H][W][Dp], lane-chunk order) to L ([H][W][D] uint16, natural order).
+cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,
+                             cudaStream_t s);
+cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D, bool wide,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
                        uint16_t *dbg_sum, cudaStream_t s);
 cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, cudaStream_t s);

@@ -4,17 +4,19 @@
 // One CTA per image row.  The planes share the aggregation kernel's layout
 // (all planes of a pixel back to back): LPS lanes hold a pixel's
 // disparities, DPL per lane, so a warp covers G = 32 / LPS neighbouring
-// pixels.  A lane loads its DPL-byte chunk of every plane at fixed offsets
-// from one pointer, one pixel group ahead of its use (register double
-// buffer), unpacks each into DPL/2 packed 16-bit pairs (d+k, d+k+DPL/2) with
-// masks and byte-permutes and adds them: S <= 8 * 255 fits 16 bits and no
-// half carries.  For each disparity it forms the key (S << 8) | d; the left
-// winner is the minimum key over the pixel's lanes (ties go to the smallest
-// d, which sits in the low bits), and every key is folded into slot x - d of
-// a shared-memory array with atomicMin, which leaves
+// pixels.  A lane loads its chunk of every plane (8 bytes of 8-bit path
+// costs, or 16 bytes of 16-bit ones) at fixed offsets from one pointer, one
+// pixel group ahead of its use (register double buffer), turns each into
+// DPL/2 packed 16-bit pairs (d+k, d+k+DPL/2) (masks and byte-permutes for
+// 8-bit planes; 16-bit planes are stored that way) and adds them.  No half
+// carries: S <= 8 * 255 for 8-bit planes, and the host bounds the 16-bit
+// path costs so that their sum fits 16 bits.  For each disparity it forms the
+// key (S << 8) | d; the left winner is the minimum key over the pixel's lanes
+// (ties go to the smallest d, which sits in the low bits), and every key is
+// folded into slot x - d of a shared-memory array with atomicMin, which leaves
 // D_right(x') = argmin_d S(x' + d, d) with the same tie rule.  After a CTA
 // barrier the row's LR check runs from shared memory.  HBM traffic: the
-// planes once (npaths * Dp bytes per pixel) plus 1 byte written per pixel.
+// planes once (npaths * Dp path costs per pixel) plus 1 byte written per pixel.
 #include "sgm_internal.cuh"
 
 namespace sgm {
@@ -51,15 +53,18 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     return p;
 }
 
-// One lane's DPL bytes of one plane: 8 -> uint2, 16 -> uint4 (words w[0..DPL/4)).
-template <int DPL>
+// One lane's chunk of one plane: DPL bytes (8-bit path costs) or 2*DPL bytes
+// (16-bit, "wide"), loaded as 32-bit words w[0..kWords).
+template <int DPL, bool WIDE>
 struct PlaneChunk {
-    uint32_t w[DPL / 4];
+    static constexpr int kWords = WIDE ? DPL / 2 : DPL / 4;
+    static_assert(kWords == 2 || kWords == 4, "a lane chunk is 8 or 16 bytes");
+    uint32_t w[kWords];
 };
-template <int DPL>
-__device__ __forceinline__ PlaneChunk<DPL> ld_plane(const uint8_t *p, uint64_t pol) {
-    PlaneChunk<DPL> v;
-    if constexpr (DPL == 8) {
+template <int DPL, bool WIDE>
+__device__ __forceinline__ PlaneChunk<DPL, WIDE> ld_plane(const uint8_t *p, uint64_t pol) {
+    PlaneChunk<DPL, WIDE> v;
+    if constexpr (PlaneChunk<DPL, WIDE>::kWords == 2) {
         asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
                      : "=r"(v.w[0]), "=r"(v.w[1])
                      : "l"(p), "l"(pol));
@@ -86,8 +91,8 @@ __device__ __forceinline__ int visit_mask(int li) {
 // Sums the path planes of one pixel into DPL/2 packed pairs S[k] = (S(d0+k), S(d0+k+h)),
 // h = DPL/2, folds its keys into the right-disparity slots and returns its smallest key.
 // NP > 0: NP planes (compile time); NP == 0: nplanes at run time.
-template <int LPS, int DPL, int NP, bool RAGGED, bool DEBUG>
-__device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL> (&v)[kMaxPaths], int nplanes,
+template <int LPS, int DPL, bool WIDE, int NP, bool RAGGED, bool DEBUG>
+__device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL, WIDE> (&v)[kMaxPaths], int nplanes,
                                                bool active, int x, int y, int W, int D, int li,
                                                uint32_t *key_right, uint16_t *dbg_sum) {
     constexpr int NR = DPL / 2;
@@ -97,10 +102,15 @@ __device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL> (&v)[kMaxPa
 #pragma unroll
     for (int q = 0; q < (NP > 0 ? NP : kMaxPaths); q++)
         if (NP > 0 || q < nplanes) {
+            if constexpr (WIDE) {
 #pragma unroll
-            for (int w = 0; w < DPL / 4; w++) {
-                S[2 * w] += v[q].w[w] & kLo;
-                S[2 * w + 1] += __byte_perm(v[q].w[w], 0u, 0x4341);
+                for (int k = 0; k < NR; k++) S[k] += v[q].w[k];  // stored as (d+k, d+k+h)
+            } else {
+#pragma unroll
+                for (int w = 0; w < DPL / 4; w++) {
+                    S[2 * w] += v[q].w[w] & kLo;
+                    S[2 * w + 1] += __byte_perm(v[q].w[w], 0u, 0x4341);
+                }
             }
         }
     const int d0 = DPL * li;
@@ -142,13 +152,14 @@ __device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL> (&v)[kMaxPa
     return best;
 }
 
-template <int LPS, int DPL, int NP, bool RAGGED, bool DEBUG>
+template <int LPS, int DPL, bool WIDE, int NP, bool RAGGED, bool DEBUG>
 __global__ void __launch_bounds__(kThreads)
     wta_kernel(const uint8_t *__restrict__ planes, int nplanes, int W, int H,
                int D, int tol, uint8_t *__restrict__ disp_lr, uint8_t *__restrict__ dbg_left,
                uint8_t *__restrict__ dbg_right, uint16_t *__restrict__ dbg_sum) {
     constexpr int G = 32 / LPS;
     constexpr int Dp = DPL * LPS;
+    constexpr int EB = WIDE ? 2 : 1;  // bytes per path cost
     constexpr int NQ = NP > 0 ? NP : kMaxPaths;
     extern __shared__ uint32_t smem[];
     uint32_t *key_right = smem;                                // W keys
@@ -158,30 +169,30 @@ __global__ void __launch_bounds__(kThreads)
     const int grp = lane / LPS, li = lane % LPS;
     for (int i = threadIdx.x; i < W; i += kThreads) key_right[i] = 0xFFFFFFFFu;
     __syncthreads();
-    // pixel records hold all planes of a pixel back to back: nplanes * Dp bytes
+    // pixel records hold all planes of a pixel back to back: nplanes * Dp * EB bytes
     const int np = NP > 0 ? NP : nplanes;
-    const size_t rec = (size_t)np * Dp;
-    const uint8_t *row = planes + (size_t)y * W * rec + DPL * li;
+    const size_t rec = (size_t)np * Dp * EB;
+    const uint8_t *row = planes + (size_t)y * W * rec + DPL * EB * li;
     const uint64_t pol = policy_evict_first();
     const int stride = nwarps * G;
     // software pipeline: the next pixel group's planes are loaded while the
     // current one is reduced
-    PlaneChunk<DPL> cur[kMaxPaths], nxt[kMaxPaths];
+    PlaneChunk<DPL, WIDE> cur[kMaxPaths], nxt[kMaxPaths];
     int x = warp * G + grp;
 #pragma unroll
     for (int q = 0; q < kMaxPaths; q++)
 #pragma unroll
-        for (int w = 0; w < DPL / 4; w++) cur[q].w[w] = nxt[q].w[w] = 0u;
+        for (int w = 0; w < PlaneChunk<DPL, WIDE>::kWords; w++) cur[q].w[w] = nxt[q].w[w] = 0u;
 #pragma unroll
     for (int q = 0; q < NQ; q++)
-        if ((NP > 0 || q < np) && x < W) cur[q] = ld_plane<DPL>(row + (size_t)x * rec + q * Dp, pol);
+        if ((NP > 0 || q < np) && x < W) cur[q] = ld_plane<DPL, WIDE>(row + (size_t)x * rec + q * Dp * EB, pol);
     for (int xb = warp * G; xb < W; xb += stride) {
         const int xn = x + stride;
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            if ((NP > 0 || q < np) && xn < W) nxt[q] = ld_plane<DPL>(row + (size_t)xn * rec + q * Dp, pol);
+            if ((NP > 0 || q < np) && xn < W) nxt[q] = ld_plane<DPL, WIDE>(row + (size_t)xn * rec + q * Dp * EB, pol);
         const bool active = x < W;
-        uint32_t best = pixel_keys<LPS, DPL, NP, RAGGED, DEBUG>(cur, np, active, x, y, W, D, li, key_right, dbg_sum);
+        uint32_t best = pixel_keys<LPS, DPL, WIDE, NP, RAGGED, DEBUG>(cur, np, active, x, y, W, D, li, key_right, dbg_sum);
         best = group_min<LPS>(best, lane);
         if (li == 0 && active) dl_row[x] = (uint8_t)(best & 0xFFu);
 #pragma unroll
@@ -209,40 +220,48 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-}  // namespace
-
-cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D,
-                       int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
-                       uint16_t *dbg_sum, cudaStream_t s) {
-    const size_t smem = (size_t)W * sizeof(uint32_t) + (size_t)((W + 3) & ~3);
-#define SGM_WTA4(L, P, N, R, G) wta_kernel<L, P, N, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
-#define SGM_WTA(L, P)                                    \
+template <bool WIDE>
+void launch_wta_t(const uint8_t *planes, int nplanes, int W, int H, int D, int tol, uint8_t *disp_lr,
+                  uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum, size_t smem, cudaStream_t s) {
+#define SGM_WTA4(L, N, R, G) wta_kernel<L, 8, WIDE, N, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
+#define SGM_WTA(L)                                       \
     do {                                                 \
-        const bool rag = D != (P) * (L);                 \
+        const bool rag = D != 8 * (L);                   \
         if (dbg_sum) {                                   \
-            if (rag) SGM_WTA4(L, P, 0, true, true);      \
-            else SGM_WTA4(L, P, 0, false, true);         \
+            if (rag) SGM_WTA4(L, 0, true, true);         \
+            else SGM_WTA4(L, 0, false, true);            \
         } else if (nplanes == 8) {                       \
-            if (rag) SGM_WTA4(L, P, 8, true, false);     \
-            else SGM_WTA4(L, P, 8, false, false);        \
+            if (rag) SGM_WTA4(L, 8, true, false);        \
+            else SGM_WTA4(L, 8, false, false);           \
         } else if (nplanes == 4) {                       \
-            if (rag) SGM_WTA4(L, P, 4, true, false);     \
-            else SGM_WTA4(L, P, 4, false, false);        \
+            if (rag) SGM_WTA4(L, 4, true, false);        \
+            else SGM_WTA4(L, 4, false, false);           \
         } else {                                         \
-            if (rag) SGM_WTA4(L, P, 0, true, false);     \
-            else SGM_WTA4(L, P, 0, false, false);        \
+            if (rag) SGM_WTA4(L, 0, true, false);        \
+            else SGM_WTA4(L, 0, false, false);           \
         }                                                \
     } while (0)
     switch (lanes_per_scanline(D)) {
-        case 1: SGM_WTA(1, 8); break;
-        case 2: SGM_WTA(2, 8); break;
-        case 4: SGM_WTA(4, 8); break;
-        case 8: SGM_WTA(8, 8); break;
-        case 16: SGM_WTA(16, 8); break;
-        default: SGM_WTA(32, 8); break;
+        case 1: SGM_WTA(1); break;
+        case 2: SGM_WTA(2); break;
+        case 4: SGM_WTA(4); break;
+        case 8: SGM_WTA(8); break;
+        case 16: SGM_WTA(16); break;
+        default: SGM_WTA(32); break;
     }
 #undef SGM_WTA4
 #undef SGM_WTA
+}
+
+}  // namespace
+
+cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D, bool wide,
+                       int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
+                       uint16_t *dbg_sum, cudaStream_t s) {
+    if (disparities_per_lane(D) != 8) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)W * sizeof(uint32_t) + (size_t)((W + 3) & ~3);
+    if (wide) launch_wta_t<true>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum, smem, s);
+    else launch_wta_t<false>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum, smem, s);
     return cudaGetLastError();
 }
 

@@ -214,6 +214,7 @@ class Workload:
     lr_tol: int
     median_k: int
     uv: bool
+    cost: int = 0  # 0: census Hamming distance, 1: SAD over the same window
 
     @property
     def de_per_frame(self) -> int:
@@ -233,8 +234,12 @@ HD_1280 = Workload("hd-1280x720-d128-census5x5-4path-uv", 1280, 720, 128, 5, 5, 
 # The paper's own setting (Sec. 4.1): 640x360, d in [0,60), 5x5 census, the four
 # streaming paths, P1=8, P2=32, 5x5 median.
 PAPER_640 = Workload("paper-640x360-d60-census5x5-stream4", 640, 360, 60, 5, 5, PATHS_STREAM4, 8, 32, 1, 5, True)
+# The same setting with the paper's other matching cost (Sec. 4.1): 5x5 SAD,
+# P1=200, P2=800.
+PAPER_640_SAD = Workload("paper-640x360-d60-sad5x5-stream4", 640, 360, 60, 5, 5, PATHS_STREAM4, 200, 800,
+                         1, 5, True, cost=1)
 
-WORKLOADS = {w.name: w for w in (SMALL_320, KITTI_1242, HD_1280, PAPER_640)}
+WORKLOADS = {w.name: w for w in (SMALL_320, KITTI_1242, HD_1280, PAPER_640, PAPER_640_SAD)}
 
 
 def scene_for(w: Workload, seed: int) -> Scene:
@@ -248,7 +253,7 @@ def scene_for(w: Workload, seed: int) -> Scene:
     if w is HD_1280:
         return ground_scene(w.W, w.H, w.D, seed, n_obstacles=10,
                             bands=[(20, 30), (50, 60), (90, 100)], texture="blur", sigma=1.0)
-    if w is PAPER_640:
+    if w is PAPER_640 or w is PAPER_640_SAD:
         return boxes_scene(w.W, w.H, w.D, seed, n_boxes=4, background=4, dlo=4, dhi=55,
                            texture="blur", sigma=1.0)
     return ground_scene(w.W, w.H, w.D, seed, n_obstacles=6, dlo=max(1, w.D // 6),

@@ -24,6 +24,8 @@ SGM_INVALID = 0xFF
 SGM_PATHS_4 = 0x0F
 SGM_PATHS_8 = 0xFF
 SGM_PATHS_STREAM4 = 0x55
+SGM_COST_CENSUS = 0  # Hamming distance of census codes over the window
+SGM_COST_SAD = 1  # sum of absolute differences over the window (16-bit path costs)
 
 STAGES = ("census", "cost", "aggregate", "wta_lr", "median", "uvmap")
 
@@ -38,7 +40,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("census_w", ctypes.c_int), ("census_h", ctypes.c_int),
                 ("path_mask", ctypes.c_int), ("P1", ctypes.c_int), ("P2", ctypes.c_int),
                 ("lr_tolerance", ctypes.c_int), ("median_k", ctypes.c_int),
-                ("row_pitch", ctypes.c_int)]
+                ("row_pitch", ctypes.c_int), ("cost", ctypes.c_int)]
 
 
 @dataclass
@@ -51,10 +53,11 @@ class SgmParams:
     lr_tolerance: int = 1
     median_k: int = 5
     row_pitch: int = 0
+    cost: int = SGM_COST_CENSUS
 
     def _c(self) -> _Params:
         return _Params(self.census_w, self.census_h, self.path_mask, self.P1, self.P2,
-                       self.lr_tolerance, self.median_k, self.row_pitch)
+                       self.lr_tolerance, self.median_k, self.row_pitch, self.cost)
 
 
 class _UvPost(ctypes.Structure):
@@ -288,7 +291,7 @@ def sgm_debug_path(h: Handle, r: int, left, right, L, stream=None):
     shp = h._img_shape()
     _check(load().sgm_debug_path(
         h.ptr, r, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
-        _dev(L, ("uint8",), (h.H, h.W, h.D), "L"), _stream(stream)), "sgm_debug_path")
+        _dev(L, ("uint16", "int16"), (h.H, h.W, h.D), "L"), _stream(stream)), "sgm_debug_path")
 
 
 def sgm_debug_sum(h: Handle, left, right, S, stream=None):

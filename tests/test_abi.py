@@ -64,6 +64,13 @@ def _create(W, H, D, **kw):
     (10, 10, 16, dict(median_k=9), sgm.SGM_ERR_UNSUPPORTED),
     (10, 10, 16, dict(row_pitch=5), sgm.SGM_ERR_INVALID_ARG),
     (9000, 10, 16, {}, sgm.SGM_ERR_UNSUPPORTED),
+    (10, 10, 16, dict(cost=2), sgm.SGM_ERR_INVALID_ARG),  # no such cost
+    # SAD: (25 * 255 + 800) * 8 paths = 57400 fits 16 bits; with P2 = 2000, 67000 does not
+    (10, 10, 16, dict(cost=1, census_w=5, census_h=5, P1=200, P2=2000), sgm.SGM_ERR_UNSUPPORTED),
+    # SAD: one path, 11 x 13 window: 36465 + 0 is above the 0x7FFF padding marker
+    (10, 10, 16, dict(cost=1, census_w=11, census_h=13, P1=0, P2=0, path_mask=1), sgm.SGM_ERR_UNSUPPORTED),
+    (10, 10, 16, dict(cost=1, census_w=17, census_h=1, P1=0, P2=0, path_mask=1), sgm.SGM_ERR_UNSUPPORTED),
+    (10, 10, 16, dict(cost=1, census_w=4, census_h=5), sgm.SGM_ERR_INVALID_ARG),  # even window
 ])
 def test_create_rejects_bad_arguments_on_host(W, H, D, kw, want):
     rc, h = _create(W, H, D, **kw)

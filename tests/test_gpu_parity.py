@@ -24,9 +24,9 @@ def u16(t):
     return t.cpu().numpy().view(np.uint16)
 
 
-def params(cw, ch, mask, P1, P2, tol, k, pitch=0):
+def params(cw, ch, mask, P1, P2, tol, k, pitch=0, cost=sgm.SGM_COST_CENSUS):
     return sgm.SgmParams(census_w=cw, census_h=ch, path_mask=mask, P1=P1, P2=P2,
-                         lr_tolerance=tol, median_k=k, row_pitch=pitch)
+                         lr_tolerance=tol, median_k=k, row_pitch=pitch, cost=cost)
 
 
 def gpu_all(left, right, D, p):
@@ -34,17 +34,18 @@ def gpu_all(left, right, D, p):
     out = {}
     with sgm.Handle(W, H, D, p) as h:
         L, R = cuda(left), cuda(right)
-        cl = torch.empty((H, W), dtype=torch.int64, device="cuda")
-        cr = torch.empty_like(cl)
-        sgm.sgm_debug_census(h, L, R, cl, cr)
-        out["codes_l"] = cl.cpu().numpy().view(np.uint64)
-        out["codes_r"] = cr.cpu().numpy().view(np.uint64)
+        if p.cost == sgm.SGM_COST_CENSUS:
+            cl = torch.empty((H, W), dtype=torch.int64, device="cuda")
+            cr = torch.empty_like(cl)
+            sgm.sgm_debug_census(h, L, R, cl, cr)
+            out["codes_l"] = cl.cpu().numpy().view(np.uint64)
+            out["codes_r"] = cr.cpu().numpy().view(np.uint64)
         out["paths"] = {}
         for r in range(8):
             if (p.path_mask >> r) & 1:
-                Lr = torch.empty((H, W, D), dtype=torch.uint8, device="cuda")
+                Lr = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
                 sgm.sgm_debug_path(h, r, L, R, Lr)
-                out["paths"][r] = Lr.cpu().numpy()
+                out["paths"][r] = u16(Lr)
         S = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
         sgm.sgm_debug_sum(h, L, R, S)
         out["S"] = u16(S)
@@ -63,8 +64,11 @@ def gpu_all(left, right, D, p):
 
 def oracle_all(left, right, D, p):
     o = oracle.sgm(left, right, D, p.census_w, p.census_h, p.path_mask, p.P1, p.P2,
-                   p.lr_tolerance, p.median_k, stages=True)
-    C = oracle.cost_volume(o["codes_l"], o["codes_r"], D, p.census_w * p.census_h - 1)
+                   p.lr_tolerance, p.median_k, stages=True, cost=p.cost)
+    if p.cost == sgm.SGM_COST_CENSUS:
+        C = oracle.cost_volume(o["codes_l"], o["codes_r"], D, p.census_w * p.census_h - 1)
+    else:
+        C = oracle.sad_cost_volume(left, right, D, p.census_w, p.census_h)
     o["paths"] = {r: oracle.aggregate_path(C, r, p.P1, p.P2)
                   for r in range(8) if (p.path_mask >> r) & 1}
     return o
@@ -80,10 +84,11 @@ def assert_same(g, o, what):
 
 def compare_all(left, right, D, p):
     g, o = gpu_all(left, right, D, p), oracle_all(left, right, D, p)
-    assert_same(g["codes_l"], o["codes_l"], "census left")
-    assert_same(g["codes_r"], o["codes_r"], "census right")
+    if p.cost == sgm.SGM_COST_CENSUS:
+        assert_same(g["codes_l"], o["codes_l"], "census left")
+        assert_same(g["codes_r"], o["codes_r"], "census right")
     for r in o["paths"]:
-        assert_same(g["paths"][r], o["paths"][r].astype(np.uint8), f"path {r}")
+        assert_same(g["paths"][r], o["paths"][r], f"path {r}")
     for k in ("S", "DL", "DR", "lr", "disp", "U", "V"):
         assert_same(g[k], o[k], k)
 
@@ -182,17 +187,17 @@ def test_row_pitch_and_side_stream():
 # ---------------------------------------------------------------------------
 
 def _workload_params(w):
-    return params(w.census_w, w.census_h, w.path_mask, w.P1, w.P2, w.lr_tol, w.median_k)
+    return params(w.census_w, w.census_h, w.path_mask, w.P1, w.P2, w.lr_tol, w.median_k, cost=w.cost)
 
 
 @pytest.mark.parametrize("name,idx", [("SMALL_320", 0), ("KITTI_1242", 1), ("HD_1280", 2),
-                                      ("PAPER_640", 5)])
+                                      ("PAPER_640", 5), ("PAPER_640_SAD", 6)])
 def test_full_size_workloads_bit_exact(name, idx):
     w = getattr(scenes, name)
     s = scenes.scene_for(w, scenes.workload_seed(idx))
     p = _workload_params(w)
     o = oracle.sgm(s.left, s.right, w.D, w.census_w, w.census_h, w.path_mask, w.P1, w.P2,
-                   w.lr_tol, w.median_k, stages=True)
+                   w.lr_tol, w.median_k, stages=True, cost=w.cost)
     with sgm.Handle(w.W, w.H, w.D, p) as h:
         L, R = cuda(s.left), cuda(s.right)
         disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
@@ -308,26 +313,76 @@ def _distorted_pair(W, H, D, seed):
     return s.left, raw, maps
 
 
-@pytest.mark.parametrize("W,H,D,cw,ch", [(96, 64, 32, 5, 5), (160, 90, 64, 9, 7), (77, 41, 16, 7, 9)])
-def test_rectified_pipeline_matches_oracle(W, H, D, cw, ch):
+@pytest.mark.parametrize("W,H,D,cw,ch,cost", [(96, 64, 32, 5, 5, 0), (160, 90, 64, 9, 7, 0),
+                                              (77, 41, 16, 7, 9, 0), (96, 64, 32, 5, 5, 1),
+                                              (83, 47, 24, 3, 7, 1)])
+def test_rectified_pipeline_matches_oracle(W, H, D, cw, ch, cost):
     left, raw, (lx, ly, rx, ry) = _distorted_pair(W, H, D, seed=W + D)
-    p = params(cw, ch, 0xFF, 4, 24, 1, 3)
+    P1, P2 = (4, 24) if cost == sgm.SGM_COST_CENSUS else (100, 400)
+    p = params(cw, ch, 0xFF, P1, P2, 1, 3, cost=cost)
     lr = oracle.rectify(left, lx, ly)
     rr = oracle.rectify(raw, rx, ry)
-    o = oracle.sgm(lr, rr, D, cw, ch, 0xFF, 4, 24, 1, 3, stages=True)
+    o = oracle.sgm(lr, rr, D, cw, ch, 0xFF, P1, P2, 1, 3, stages=True, cost=cost)
     with sgm.Handle(W, H, D, p) as h:
         maps = [cuda(m.view(np.int16)) for m in (lx, ly, rx, ry)]
         sgm.sgm_set_rectification(h, *maps)
-        cl = torch.empty((H, W), dtype=torch.int64, device="cuda")
-        cr = torch.empty_like(cl)
-        sgm.sgm_debug_census(h, cuda(left), cuda(raw), cl, cr)
         disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        if cost == sgm.SGM_COST_CENSUS:
+            cl = torch.empty((H, W), dtype=torch.int64, device="cuda")
+            cr = torch.empty_like(cl)
+            sgm.sgm_debug_census(h, cuda(left), cuda(raw), cl, cr)
+            torch.cuda.synchronize()
+            assert_same(cl.cpu().numpy().view(np.uint64), o["codes_l"], "census left")
+            assert_same(cr.cpu().numpy().view(np.uint64), o["codes_r"], "census right")
+        S = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
+        sgm.sgm_debug_sum(h, cuda(left), cuda(raw), S)
         h.compute(cuda(left), cuda(raw), disp)
         torch.cuda.synchronize()
-        assert_same(cl.cpu().numpy().view(np.uint64), o["codes_l"], "census left")
-        assert_same(cr.cpu().numpy().view(np.uint64), o["codes_r"], "census right")
+        assert_same(u16(S), o["S"], "S")
         assert_same(disp.cpu().numpy(), o["disp"], "disp")
         sgm.sgm_set_rectification(h)  # off again: plain images
         h.compute(cuda(lr), cuda(rr), disp)
         torch.cuda.synchronize()
         assert_same(disp.cpu().numpy(), o["disp"], "disp without maps")
+
+
+# --------------------------------------------------------------------------
+# SAD matching cost (16-bit costs and path costs)
+# --------------------------------------------------------------------------
+
+SAD_CASES = [
+    # W, H, D, window, path mask, P1, P2, LR tol, median
+    (37, 23, 16, 5, 5, 0x0F, 200, 800, 1, 5),
+    (64, 33, 60, 5, 5, 0x55, 200, 800, 1, 5),     # the paper's paths, ragged D
+    (129, 40, 128, 5, 5, 0xFF, 200, 800, 1, 3),   # S up to 8 * 7175 = 57400
+    (70, 45, 100, 3, 3, 0xAA, 50, 300, 1, 3),
+    (5, 100, 33, 7, 5, 0x0F, 10, 60, 2, 7),
+    (300, 20, 255, 5, 5, 0x03, 200, 800, 1, 3),   # D = 255: 32 lanes per pixel
+    (1, 1, 1, 1, 1, 0x01, 0, 0, -1, 0),
+    (200, 1, 32, 5, 5, 0x0F, 200, 800, 1, 3),
+    (45, 31, 2, 11, 11, 0x01, 0, 0, 0, 3),        # costs up to 30855
+    (97, 61, 100, 1, 1, 0x3C, 20, 100, 1, 1),
+]
+
+
+@pytest.mark.parametrize("case", SAD_CASES, ids=lambda c: "x".join(map(str, c[:3])) + f"-w{c[3]}x{c[4]}")
+def test_sad_stage_parity(case):
+    W, H, D, ww, wh, mask, P1, P2, tol, k = case
+    if min(W, H) >= 8:
+        s = scenes.boxes_scene(W, H, D, seed=W * 7 + H, n_boxes=3, dlo=min(2, D - 1), dhi=max(2, D - 1))
+        left, right = s.left, s.right
+    else:
+        r = np.random.default_rng(W + 3 * H + D)
+        left = r.integers(0, 256, (H, W)).astype(np.uint8)
+        right = r.integers(0, 256, (H, W)).astype(np.uint8)
+    compare_all(left, right, D, params(ww, wh, mask, P1, P2, tol, k, cost=sgm.SGM_COST_SAD))
+
+
+def test_sad_handle_has_no_census_codes():
+    p = params(5, 5, 0x0F, 200, 800, 1, 3, cost=sgm.SGM_COST_SAD)
+    with sgm.Handle(16, 8, 8, p) as h:
+        img = torch.zeros((8, 16), dtype=torch.uint8, device="cuda")
+        c = torch.empty((8, 16), dtype=torch.int64, device="cuda")
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_debug_census(h, img, img, c, c)
+        assert e.value.status == sgm.SGM_ERR_UNSUPPORTED

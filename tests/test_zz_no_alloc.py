@@ -20,16 +20,17 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 CASES = [
-    # W, H, D, census, path mask, P1, P2, LR tol, median
-    (320, 240, 64, (5, 5), sgm.SGM_PATHS_4, 4, 24, 1, 5),
-    (200, 150, 32, (9, 7), sgm.SGM_PATHS_8, 8, 96, 1, 3),
+    # W, H, D, window, path mask, P1, P2, LR tol, median, cost
+    (320, 240, 64, (5, 5), sgm.SGM_PATHS_4, 4, 24, 1, 5, sgm.SGM_COST_CENSUS),
+    (200, 150, 32, (9, 7), sgm.SGM_PATHS_8, 8, 96, 1, 3, sgm.SGM_COST_CENSUS),
+    (160, 120, 48, (5, 5), sgm.SGM_PATHS_STREAM4, 200, 800, 1, 5, sgm.SGM_COST_SAD),
 ]
 
 
-def _run_both(W, H, D, cw_ch, mask, P1, P2, tol, k, seed):
+def _run_both(W, H, D, cw_ch, mask, P1, P2, tol, k, cost, seed):
     s = scenes.boxes_scene(W, H, D, seed=seed, n_boxes=3, dlo=2, dhi=D - 2)
     p = sgm.SgmParams(census_w=cw_ch[0], census_h=cw_ch[1], path_mask=mask, P1=P1, P2=P2,
-                      lr_tolerance=tol, median_k=k)
+                      lr_tolerance=tol, median_k=k, cost=cost)
     left = torch.from_numpy(s.left).cuda()
     right = torch.from_numpy(s.right).cuda()
     want = torch.empty((H, W), dtype=torch.uint8, device="cuda")
@@ -46,7 +47,7 @@ def test_static_matches_handle_path_on_consecutive_calls():
         s, p, got, want = _run_both(*case, seed=90 + i)
         assert np.array_equal(got, want), f"call {i}: differs from sgm_compute"
         ref = oracle.sgm(s.left, s.right, case[2], p.census_w, p.census_h, p.path_mask, p.P1, p.P2,
-                         p.lr_tolerance, p.median_k, uv=False)
+                         p.lr_tolerance, p.median_k, uv=False, cost=p.cost)
         assert np.array_equal(got, ref["disp"]), f"call {i}: differs from the oracle"
 
 

@@ -46,3 +46,19 @@ def test_two_ranks_max_time_and_distinct_pairs():
     assert out[0][1] != out[1][1]          # each rank draws its own pair
     assert out[0][2] == out[1][2] == 2.0   # max over ranks
     assert out[0][3] == out[1][3] == 100.0  # 2 ranks x 100 units / 2 s
+
+
+def test_oracle_pool_runs_one_band_per_process():
+    """The all-cores CPU baseline: spawned processes each run the unchanged
+    oracle on the same band and report the work done."""
+    import bench
+    from paper_1807_06271_gb300 import scenes
+    w = scenes.SMALL_320
+    scene = scenes.scene_for(w, scenes.workload_seed(0))
+    pool = bench.OraclePool(procs=2)
+    try:
+        dt, de = pool.run(w, scene, 16, 1)
+    finally:
+        pool.close()
+    assert pool.procs == 2 and dt > 0
+    assert de == 2 * w.W * 16 * w.D

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                      uint32_t P1x2, uint32_t P2x2, PathJobs jobs,
                      typename Lane<DPL, WIDE>::T *__restrict__ planes, int nplanes,
                      unsigned *__restrict__ job_counter) {
+    wait_for_predecessor();
     using CT = typename Lane<DPL, WIDE>::T;
     constexpr int G = 32 / LPS, NR = DPL / 2;
     const int lane = threadIdx.x & 31;
@@ -411,11 +412,9 @@ cudaError_t launch_lps(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, 
     constexpr int PF = sizeof(CT) == 8 ? 16 : 8;
     const CT *c = reinterpret_cast<const CT *>(cost);
     CT *p = reinterpret_cast<CT *>(planes);
-    if (D == DPL * LPS)
-        aggregate_kernel<LPS, DPL, WIDE, false, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
-    else
-        aggregate_kernel<LPS, DPL, WIDE, true, PF><<<blocks, kWarps * 32, 0, s>>>(c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter);
-    return cudaGetLastError();
+    auto kernel = D == DPL * LPS ? aggregate_kernel<LPS, DPL, WIDE, false, PF> : aggregate_kernel<LPS, DPL, WIDE, true, PF>;
+    return launch_k(kernel, dim3(blocks), dim3(kWarps * 32), 0, s, c, W, H, D, P1x2, P2x2, jobs, p, nplanes,
+                    job_counter);
 }
 
 template <bool WIDE>
@@ -437,6 +436,7 @@ cudaError_t launch_all(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, 
 // Plane 0 ([H][W][Dp], lane-chunk order) -> L ([H][W][D] uint16, natural order).
 __global__ void unpermute_kernel(const uint8_t *__restrict__ plane, int npx, int D, int Dp, int dpl,
                                  bool wide, uint16_t *__restrict__ L) {
+    wait_for_predecessor();
     const size_t n = (size_t)npx * D;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t p = i / D;
@@ -458,10 +458,8 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
                              unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
     if (jobs.jbegin[jobs.n] == 0) return cudaSuccess;
     if (disparities_per_lane(D) != 8) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(job_counter, 0, kJobStateBytes, s);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int blocks = sms * (blocks_per_sm > 0 ? blocks_per_sm : 2);

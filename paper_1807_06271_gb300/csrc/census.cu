@@ -28,6 +28,7 @@ template <typename CodeT, int CW, int CH, bool RECT>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
                   int W, int H, CodeT *__restrict__ codes, RectMaps maps) {
+    wait_for_predecessor();
     constexpr int TW = kBX + CW - 1, TH = kBY * kRows + CH - 1;
     constexpr int RX = CW / 2, RY = CH / 2;
     __shared__ uint8_t tile[TH][TW];
@@ -79,6 +80,7 @@ template <typename CodeT, bool RECT>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel_any(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
                       int W, int H, int cw, int ch, CodeT *__restrict__ codes, RectMaps maps) {
+    wait_for_predecessor();
     extern __shared__ uint16_t tile_any[];
     const int TW = kBX + cw - 1, TH = kBY + ch - 1;
     const int rx = cw / 2, ry = ch / 2;
@@ -147,7 +149,10 @@ __device__ __forceinline__ void st_shared_chunk(uint8_t *p, const uint32_t (&w)[
 template <typename CodeT, int DPL, bool RAGGED>
 __global__ void __launch_bounds__(kCostThreads)
     cost_kernel(const CodeT *__restrict__ codes, int W, int H, int D, int Dp, int nbits,
-                uint8_t *__restrict__ cost) {
+                uint8_t *__restrict__ cost, unsigned *__restrict__ job_state) {
+    wait_for_predecessor();
+    if (job_state && blockIdx.x == 0 && blockIdx.y == 0)
+        for (int i = threadIdx.x; i < (int)(kJobStateBytes / sizeof(unsigned)); i += kCostThreads) job_state[i] = 0u;
     using VecT = typename std::conditional<DPL == 8, uint2, uint4>::type;
     extern __shared__ __align__(16) unsigned char cost_smem[];
     const int stride = Dp + DPL;  // padded tile row (bytes)
@@ -240,27 +245,21 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
     dim3 block(kBX, kBY), grid((W + kBX - 1) / kBX, (H + kBY - 1) / kBY, 2);
     const dim3 grid4((W + kBX - 1) / kBX, (H + kBY * kRows - 1) / (kBY * kRows), 2);
     const bool rect = maps.lx != nullptr;
-#define SGM_CENSUS(T, CWv, CHv)                                                                         \
-    do {                                                                                                \
-        if (rect) census_kernel<T, CWv, CHv, true><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (T *)codes, maps);  \
-        else census_kernel<T, CWv, CHv, false><<<grid4, block, 0, s>>>(left, right, pitch, W, H, (T *)codes, maps);      \
-    } while (0)
-    if (cw == 5 && ch == 5 && code_bytes == 4)
-        SGM_CENSUS(uint32_t, 5, 5);
-    else if (cw == 9 && ch == 7 && code_bytes == 8)
-        SGM_CENSUS(uint64_t, 9, 7);
-    else {
-        size_t smem = (size_t)(kBX + cw - 1) * (kBY + ch - 1) * sizeof(uint16_t);
-        if (code_bytes == 4) {
-            if (rect) census_kernel_any<uint32_t, true><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint32_t *)codes, maps);
-            else census_kernel_any<uint32_t, false><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint32_t *)codes, maps);
-        } else {
-            if (rect) census_kernel_any<uint64_t, true><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint64_t *)codes, maps);
-            else census_kernel_any<uint64_t, false><<<grid, block, smem, s>>>(left, right, pitch, W, H, cw, ch, (uint64_t *)codes, maps);
-        }
-    }
+#define SGM_CENSUS(T, CWv, CHv)                                                                                     \
+    (rect ? launch_k(census_kernel<T, CWv, CHv, true>, grid4, block, 0, s, left, right, pitch, W, H, (T *)codes, maps) \
+          : launch_k(census_kernel<T, CWv, CHv, false>, grid4, block, 0, s, left, right, pitch, W, H, (T *)codes, maps))
+    if (cw == 5 && ch == 5 && code_bytes == 4) return SGM_CENSUS(uint32_t, 5, 5);
+    if (cw == 9 && ch == 7 && code_bytes == 8) return SGM_CENSUS(uint64_t, 9, 7);
 #undef SGM_CENSUS
-    return cudaGetLastError();
+    const size_t smem = (size_t)(kBX + cw - 1) * (kBY + ch - 1) * sizeof(uint16_t);
+    if (code_bytes == 4) {
+        uint32_t *c = (uint32_t *)codes;
+        return rect ? launch_k(census_kernel_any<uint32_t, true>, grid, block, smem, s, left, right, pitch, W, H, cw, ch, c, maps)
+                    : launch_k(census_kernel_any<uint32_t, false>, grid, block, smem, s, left, right, pitch, W, H, cw, ch, c, maps);
+    }
+    uint64_t *c = (uint64_t *)codes;
+    return rect ? launch_k(census_kernel_any<uint64_t, true>, grid, block, smem, s, left, right, pitch, W, H, cw, ch, c, maps)
+                : launch_k(census_kernel_any<uint64_t, false>, grid, block, smem, s, left, right, pitch, W, H, cw, ch, c, maps);
 }
 
 }  // namespace sgm
@@ -268,7 +267,7 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
 namespace sgm {
 
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
-                        uint8_t *cost, cudaStream_t s) {
+                        uint8_t *cost, unsigned *job_state, cudaStream_t s) {
     const int Dp = padded_disparities(D), dpl = disparities_per_lane(D);
     const size_t smem = (((size_t)kSeg * (Dp + dpl) + 15) & ~(size_t)15) + (size_t)(2 * kSeg + Dp + 2) * code_bytes;
     const dim3 grid((W + kSeg - 1) / kSeg, H);
@@ -278,7 +277,9 @@ cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, 
     do {                                                                                                         \
         e = cudaFuncSetAttribute(cost_kernel<T, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                          \
-        cost_kernel<T, P, R><<<grid, kCostThreads, smem, s>>>((const T *)codes, W, H, D, Dp, nbits, cost);        \
+        e = launch_k(cost_kernel<T, P, R>, grid, dim3(kCostThreads), smem, s, (const T *)codes, W, H, D, Dp,   \
+                     nbits, cost, job_state);                                                                    \
+        if (e != cudaSuccess) return e;                                                                          \
     } while (0)
 #define SGM_COST2(T, P)                \
     do {                               \

@@ -81,20 +81,20 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     uint8_t *disp_lr = base + lr_off;
     const sgm::PathJobs jobs = sgm::make_path_jobs(W, H, D, params->path_mask);
 
-    // Every kernel below overwrites the scratch it later reads, and the job
-    // counter is cleared on the stream before the aggregation kernel, so
-    // nothing left by an earlier call needs clearing.
+    // Every kernel below overwrites the scratch it later reads, and the cost
+    // kernel clears the aggregation's work-queue state, so nothing left by an
+    // earlier call needs clearing.
     cudaStream_t s = (cudaStream_t)stream;
     const int pitch = params->row_pitch ? params->row_pitch : W;
     const sgm::RectMaps no_maps{nullptr, nullptr, nullptr, nullptr};
     cudaError_t e;
     if (wide) {
         e = sgm::launch_sad_cost(left, right, pitch, W, H, D, params->census_w, params->census_h, no_maps,
-                                 reinterpret_cast<uint16_t *>(cost), s);
+                                 reinterpret_cast<uint16_t *>(cost), counter, s);
     } else {
         e = sgm::launch_census(left, right, pitch, W, H, params->census_w, params->census_h, code_bytes,
                                codes, no_maps, s);
-        if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, s);
+        if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, counter, s);
     }
     if (e == cudaSuccess)
         e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, wide, jobs, planes, npaths,

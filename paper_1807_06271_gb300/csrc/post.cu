@@ -51,6 +51,7 @@ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 
 template <int K>
 __global__ void __launch_bounds__(kMX *kMY)
     median_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int W, int H) {
+    wait_for_predecessor();
     constexpr int R = K / 2, TW = kMX + K - 1, TH = kMY + K - 1;
     constexpr int N = K * K, NP = pow2_at_least(N);
     __shared__ uint8_t tile[TH][TW];
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kUVThreads)
     uvmap_kernel(const uint8_t *__restrict__ disp, int W, int H, int D, int ustrips,
                  uint16_t *__restrict__ umap, uint16_t *__restrict__ vmap) {
     extern __shared__ uint32_t hist[];
+    wait_for_predecessor();
     if ((int)blockIdx.x < ustrips) {
         const int x0 = blockIdx.x * 32;
         const int col = threadIdx.x & 31, phase = threadIdx.x >> 5, nphase = kUVThreads / 32;
@@ -124,20 +126,19 @@ __global__ void __launch_bounds__(kUVThreads)
 cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, cudaStream_t s) {
     dim3 block(kMX, kMY), grid((W + kMX - 1) / kMX, (H + kMY - 1) / kMY);
     switch (k) {
-        case 3: median_kernel<3><<<grid, block, 0, s>>>(in, out, W, H); break;
-        case 5: median_kernel<5><<<grid, block, 0, s>>>(in, out, W, H); break;
-        case 7: median_kernel<7><<<grid, block, 0, s>>>(in, out, W, H); break;
+        case 3: return launch_k(median_kernel<3>, grid, block, 0, s, in, out, W, H);
+        case 5: return launch_k(median_kernel<5>, grid, block, 0, s, in, out, W, H);
+        case 7: return launch_k(median_kernel<7>, grid, block, 0, s, in, out, W, H);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_uvmap(const uint8_t *disp, int W, int H, int D, uint16_t *umap, uint16_t *vmap,
                          cudaStream_t s) {
     const int ustrips = (W + 31) / 32, vblocks = (H + kVRows - 1) / kVRows;
     const size_t smem = (size_t)(D * 32 > kVRows * D ? D * 32 : kVRows * D) * sizeof(uint32_t);
-    uvmap_kernel<<<ustrips + vblocks, kUVThreads, smem, s>>>(disp, W, H, D, ustrips, umap, vmap);
-    return cudaGetLastError();
+    return launch_k(uvmap_kernel, dim3(ustrips + vblocks), dim3(kUVThreads), smem, s, disp, W, H, D, ustrips,
+                    umap, vmap);
 }
 
 }  // namespace sgm

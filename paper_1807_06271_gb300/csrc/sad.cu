@@ -63,8 +63,11 @@ template <bool RECT>
 __global__ void __launch_bounds__(kThreads)
     sad_cost_kernel(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
                     int W, int H, int D, int Dp, int ww, int wh, RectMaps maps,
-                    uint4 *__restrict__ cost) {
+                    uint4 *__restrict__ cost, unsigned *__restrict__ job_state) {
     extern __shared__ __align__(16) unsigned char sad_smem[];
+    wait_for_predecessor();
+    if (job_state && blockIdx.x == 0 && blockIdx.y == 0)
+        for (int i = threadIdx.x; i < (int)(kJobStateBytes / sizeof(unsigned)); i += kThreads) job_state[i] = 0u;
     const int rw = ww / 2, rh = wh / 2;
     const int ncol = kSeg + 2 * rw;          // V columns (segment + halo)
     const int lcols = ncol, rcols = kSeg + Dp - 1 + 2 * rw;
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kThreads)
 
 cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
                             int D, int ww, int wh, const RectMaps &maps, uint16_t *cost,
-                            cudaStream_t s) {
+                            unsigned *job_state, cudaStream_t s) {
     if (disparities_per_lane(D) != 8 || ww < 1 || wh < 1 || ww > kMaxSadWindow || wh > kMaxSadWindow)
         return cudaErrorInvalidValue;
     const int Dp = padded_disparities(D);
@@ -161,16 +164,11 @@ cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch
     const dim3 grid((W + kSeg - 1) / kSeg, (H + kRows - 1) / kRows);
     uint4 *out = reinterpret_cast<uint4 *>(cost);
     cudaError_t e;
-    if (maps.lx) {
-        e = cudaFuncSetAttribute(sad_cost_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        sad_cost_kernel<true><<<grid, kThreads, smem, s>>>(left, right, pitch, W, H, D, Dp, ww, wh, maps, out);
-    } else {
-        e = cudaFuncSetAttribute(sad_cost_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        sad_cost_kernel<false><<<grid, kThreads, smem, s>>>(left, right, pitch, W, H, D, Dp, ww, wh, maps, out);
-    }
-    return cudaGetLastError();
+    auto kernel = maps.lx ? sad_cost_kernel<true> : sad_cost_kernel<false>;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_k(kernel, grid, dim3(kThreads), smem, s, left, right, pitch, W, H, D, Dp, ww, wh, maps, out,
+                    job_state);
 }
 
 }  // namespace sgm

@@ -112,9 +112,9 @@ int run_cost(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaStr
     if (h->wide) {
         const int pitch = h->p.row_pitch ? h->p.row_pitch : h->W;
         e = launch_sad_cost(left, right, pitch, h->W, h->H, h->D, h->p.census_w, h->p.census_h, h->rect,
-                            reinterpret_cast<uint16_t *>(h->cost), s);
+                            reinterpret_cast<uint16_t *>(h->cost), h->job_counter, s);
     } else {
-        e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, s);
+        e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, h->job_counter, s);
     }
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;

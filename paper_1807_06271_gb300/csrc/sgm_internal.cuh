@@ -31,6 +31,29 @@ inline long scanlines_of(int r, int W, int H) {
 
 // Rectification maps of the left and right image (device, W x H each; all
 // null when the images are already rectified).
+// Programmatic dependent launch.  Every kernel of the pipeline is launched
+// with programmatic stream serialisation, so the launch of kernel k+1 overlaps
+// the end of kernel k; each kernel's first statement waits until its stream
+// predecessor has completed and its memory is visible, before it reads or
+// writes anything.  Kernels launched the ordinary way pass the wait at once.
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 struct RectMaps {
     const uint16_t *lx, *ly, *rx, *ry;
 };
@@ -149,16 +172,18 @@ namespace sgm {
 cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
                           int cw, int ch, int code_bytes, void *codes, const RectMaps &maps,
                           cudaStream_t s);
+// The cost kernels also clear job_state (kJobStateBytes, may be null), the
+// work-queue state of the aggregation kernel that follows them on the stream.
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
-                        uint8_t *cost, cudaStream_t s);
+                        uint8_t *cost, unsigned *job_state, cudaStream_t s);
 // SAD over a ww x wh window (clamped reads; rectified through maps when set) into a
 // 16-bit cost volume [H][W][Dp] in the wide lane-chunk order.
 cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
                             int D, int ww, int wh, const RectMaps &maps, uint16_t *cost,
-                            cudaStream_t s);
+                            unsigned *job_state, cudaStream_t s);
 // Planes are pixel-interleaved: [H][W][nplanes][Dp], entry k of `jobs` writing
-// plane jobs.plane[k].  job_counter (kJobStateBytes) is cleared on s before
-// the kernel starts.
+// plane jobs.plane[k].  job_counter (kJobStateBytes) must have been cleared by
+// the cost kernel launched before it on s.
 // wide: 16-bit costs and planes (SAD), else 8-bit.
 cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2, bool wide,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,

@@ -14,6 +14,7 @@ constexpr int kTX = 32, kTY = 8, kMaxR = 7;
 __global__ void __launch_bounds__(kTX *kTY)
     uvpost_kernel(const uint16_t *__restrict__ map, int rows, int cols, int threshold, int r0, int r1,
                   int c0, int c1, int rad, uint8_t *__restrict__ out) {
+    wait_for_predecessor();
     constexpr int BH = kTY + 2 * (kMaxR + 1), BW = kTX + 2 * (kMaxR + 1);
     __shared__ uint8_t bin[BH][BW];               // thresholded, halo rad + 1
     __shared__ uint8_t dil[kTY + 2][kTX + 2];     // dilated, halo 1

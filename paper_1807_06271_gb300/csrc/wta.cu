@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kThreads)
     wta_kernel(const uint8_t *__restrict__ planes, int nplanes, int W, int H,
                int D, int tol, uint8_t *__restrict__ disp_lr, uint8_t *__restrict__ dbg_left,
                uint8_t *__restrict__ dbg_right, uint16_t *__restrict__ dbg_sum) {
+    wait_for_predecessor();
     constexpr int G = 32 / LPS;
     constexpr int Dp = DPL * LPS;
     constexpr int EB = WIDE ? 2 : 1;  // bytes per path cost
@@ -221,9 +222,12 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <bool WIDE>
-void launch_wta_t(const uint8_t *planes, int nplanes, int W, int H, int D, int tol, uint8_t *disp_lr,
-                  uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum, size_t smem, cudaStream_t s) {
-#define SGM_WTA4(L, N, R, G) wta_kernel<L, 8, WIDE, N, R, G><<<H, kThreads, smem, s>>>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
+cudaError_t launch_wta_t(const uint8_t *planes, int nplanes, int W, int H, int D, int tol, uint8_t *disp_lr,
+                         uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+#define SGM_WTA4(L, N, R, G)                                                                                    \
+    e = launch_k(wta_kernel<L, 8, WIDE, N, R, G>, dim3(H), dim3(kThreads), smem, s, planes, nplanes, W, H, D, tol, \
+                 disp_lr, dbg_left, dbg_right, dbg_sum)
 #define SGM_WTA(L)                                       \
     do {                                                 \
         const bool rag = D != 8 * (L);                   \
@@ -251,6 +255,7 @@ void launch_wta_t(const uint8_t *planes, int nplanes, int W, int H, int D, int t
     }
 #undef SGM_WTA4
 #undef SGM_WTA
+    return e;
 }
 
 }  // namespace
@@ -260,9 +265,8 @@ cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D, 
                        uint16_t *dbg_sum, cudaStream_t s) {
     if (disparities_per_lane(D) != 8) return cudaErrorInvalidValue;
     const size_t smem = (size_t)W * sizeof(uint32_t) + (size_t)((W + 3) & ~3);
-    if (wide) launch_wta_t<true>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum, smem, s);
-    else launch_wta_t<false>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum, smem, s);
-    return cudaGetLastError();
+    if (wide) return launch_wta_t<true>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum, smem, s);
+    return launch_wta_t<false>(planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum, smem, s);
 }
 
 }  // namespace sgm

@@ -135,6 +135,26 @@ int uvmap_postprocess(sgm_handle h, const uint16_t *umap, const uint16_t *vmap,
 int sgm_compute_host(sgm_handle h, const uint8_t *left, const uint8_t *right,
                      uint8_t *disp, uint16_t *umap, uint16_t *vmap, void *stream);
 
+/* Pipelined form of sgm_compute_host for a stream of frames (the paper's
+ * camera loop, Sec. 3): queues the copy of left/right (host, H x W each,
+ * dense) into one of two handle-owned device slots on an internal copy
+ * stream, the pipeline on `stream` once they have arrived, and the copy of
+ * disp (and of umap/vmap when non-NULL, as in sgm_compute_host) back to the
+ * host on a second internal copy stream; returns without waiting and stores
+ * the frame's number in *ticket.  Frame t+1's upload and frame t-1's download
+ * overlap frame t's pipeline.  Until sgm_host_wait(h, *ticket) returns, the
+ * frame's left/right must stay unchanged and disp/umap/vmap must not be read.
+ * Use pinned host memory (pageable memory makes the copies synchronous).
+ * Calls on one handle must use one `stream`. */
+int sgm_compute_host_async(sgm_handle h, const uint8_t *left, const uint8_t *right,
+                           uint8_t *disp, uint16_t *umap, uint16_t *vmap, void *stream,
+                           unsigned long long *ticket);
+
+/* Wait until frame `ticket` of sgm_compute_host_async has been copied back
+ * (its inputs are then free as well).  A ticket not yet issued is
+ * SGM_ERR_INVALID_ARG. */
+int sgm_host_wait(sgm_handle h, unsigned long long ticket);
+
 /* Many pairs in one go (the method of Sec. 3.1 per pair): n handles (each
  * with its own size and parameters), device pointers left[i], right[i],
  * disp[i] and optional umap[i]/vmap[i] (umap/vmap NULL, or NULL entries, skip

@@ -180,11 +180,18 @@ void free_handle(sgm_handle_s *h) {
     cudaFree(h->job_counter);
     cudaFree(h->planes);
     cudaFree(h->disp_lr);
-    cudaFree(h->io_left);
-    cudaFree(h->io_right);
-    cudaFree(h->io_disp);
-    cudaFree(h->io_umap);
-    cudaFree(h->io_vmap);
+    for (IoSlot &sl : h->io) {
+        cudaFree(sl.left);
+        cudaFree(sl.right);
+        cudaFree(sl.disp);
+        cudaFree(sl.umap);
+        cudaFree(sl.vmap);
+        if (sl.in_ready) cudaEventDestroy(sl.in_ready);
+        if (sl.computed) cudaEventDestroy(sl.computed);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (h->h2d) cudaStreamDestroy(h->h2d);
+    if (h->d2h) cudaStreamDestroy(h->d2h);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
@@ -322,49 +329,128 @@ int uvmap_compute(sgm_handle h, const uint8_t *disp, uint16_t *umap, uint16_t *v
     return uv_on(h, disp, umap, vmap, (cudaStream_t)stream);
 }
 
+namespace {
+
+// Device buffers and events of staging slot i (first use only).
+int ensure_slot(sgm_handle_s *h, int i) {
+    IoSlot &sl = h->io[i];
+    if (sl.left) return SGM_OK;
+    const size_t npx = (size_t)h->W * h->H;
+    int rc = dev_alloc(&sl.left, npx);
+    if (rc == SGM_OK) rc = dev_alloc(&sl.right, npx);
+    if (rc == SGM_OK) rc = dev_alloc(&sl.disp, npx);
+    if (rc == SGM_OK) rc = dev_alloc(&sl.umap, (size_t)h->D * h->W * sizeof(uint16_t));
+    if (rc == SGM_OK) rc = dev_alloc(&sl.vmap, (size_t)h->H * h->D * sizeof(uint16_t));
+    if (rc == SGM_OK && (cudaEventCreateWithFlags(&sl.in_ready, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess))
+        rc = SGM_ERR_CUDA;
+    if (rc != SGM_OK) {
+        cudaFree(sl.left);
+        cudaFree(sl.right);
+        cudaFree(sl.disp);
+        cudaFree(sl.umap);
+        cudaFree(sl.vmap);
+        if (sl.in_ready) cudaEventDestroy(sl.in_ready);
+        if (sl.computed) cudaEventDestroy(sl.computed);
+        if (sl.done) cudaEventDestroy(sl.done);
+        sl = IoSlot{};
+        cudaGetLastError();
+    }
+    return rc;
+}
+
+// The pipeline on slot sl's device inputs, into its device outputs (dense images).
+int compute_slot(sgm_handle_s *h, IoSlot &sl, bool maps, cudaStream_t s) {
+    const int saved_pitch = h->p.row_pitch;
+    h->p.row_pitch = 0;
+    int rc = compute_on(h, sl.left, sl.right, sl.disp, s);
+    h->p.row_pitch = saved_pitch;
+    if (rc == SGM_OK && maps) rc = uv_on(h, sl.disp, sl.umap, sl.vmap, s);
+    return rc;
+}
+
+int copy_out(sgm_handle_s *h, const IoSlot &sl, uint8_t *disp, uint16_t *umap, uint16_t *vmap,
+             cudaStream_t s) {
+    const size_t npx = (size_t)h->W * h->H;
+    if (cudaMemcpyAsync(disp, sl.disp, npx, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SGM_ERR_CUDA;
+    if (umap && (cudaMemcpyAsync(umap, sl.umap, (size_t)h->D * h->W * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                 cudaMemcpyAsync(vmap, sl.vmap, (size_t)h->H * h->D * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+        return SGM_ERR_CUDA;
+    return SGM_OK;
+}
+
+}  // namespace
+
 int sgm_compute_host(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
                      uint16_t *umap, uint16_t *vmap, void *stream) {
     if (!h || !left || !right || !disp || (!umap) != (!vmap)) return SGM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return SGM_ERR_CUDA;
-    const size_t npx = (size_t)h->W * h->H;
-    int rc = SGM_OK;
-    if (!h->io_left) {
-        rc = dev_alloc(&h->io_left, npx);
-        if (rc == SGM_OK) rc = dev_alloc(&h->io_right, npx);
-        if (rc == SGM_OK) rc = dev_alloc(&h->io_disp, npx);
-        if (rc == SGM_OK) rc = dev_alloc(&h->io_umap, (size_t)h->D * h->W * sizeof(uint16_t));
-        if (rc == SGM_OK) rc = dev_alloc(&h->io_vmap, (size_t)h->H * h->D * sizeof(uint16_t));
-        if (rc != SGM_OK) {
-            cudaFree(h->io_left);
-            cudaFree(h->io_right);
-            cudaFree(h->io_disp);
-            cudaFree(h->io_umap);
-            cudaFree(h->io_vmap);
-            h->io_left = h->io_right = h->io_disp = nullptr;
-            h->io_umap = h->io_vmap = nullptr;
-            return rc;
-        }
-    }
+    int rc = ensure_slot(h, 0);
+    if (rc != SGM_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // The handle's own input buffers are dense (pitch W).
-    const int saved_pitch = h->p.row_pitch;
-    h->p.row_pitch = 0;
-    if (cudaMemcpyAsync(h->io_left, left, npx, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(h->io_right, right, npx, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    IoSlot &sl = h->io[0];
+    const size_t npx = (size_t)h->W * h->H;
+    // frames still in flight through sgm_compute_host_async use the slots too
+    for (IoSlot &o : h->io)
+        if (o.done && cudaStreamWaitEvent(s, o.done, 0) != cudaSuccess) rc = SGM_ERR_CUDA;
+    if (rc == SGM_OK && (cudaMemcpyAsync(sl.left, left, npx, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                         cudaMemcpyAsync(sl.right, right, npx, cudaMemcpyHostToDevice, s) != cudaSuccess))
         rc = SGM_ERR_CUDA;
-    if (rc == SGM_OK) rc = compute_on(h, h->io_left, h->io_right, h->io_disp, s);
-    h->p.row_pitch = saved_pitch;
-    if (rc == SGM_OK && umap) rc = uv_on(h, h->io_disp, h->io_umap, h->io_vmap, s);
-    if (rc == SGM_OK && cudaMemcpyAsync(disp, h->io_disp, npx, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        rc = SGM_ERR_CUDA;
-    if (rc == SGM_OK && umap) {
-        if (cudaMemcpyAsync(umap, h->io_umap, (size_t)h->D * h->W * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaMemcpyAsync(vmap, h->io_vmap, (size_t)h->H * h->D * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            rc = SGM_ERR_CUDA;
-    }
+    if (rc == SGM_OK) rc = compute_slot(h, sl, umap != nullptr, s);
+    if (rc == SGM_OK) rc = copy_out(h, sl, disp, umap, vmap, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == SGM_OK) rc = SGM_ERR_CUDA;
     return rc;
+}
+
+int sgm_compute_host_async(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                           uint16_t *umap, uint16_t *vmap, void *stream, unsigned long long *ticket) {
+    if (!h || !left || !right || !disp || !ticket || (!umap) != (!vmap)) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    int rc = ensure_slot(h, 0);
+    if (rc == SGM_OK) rc = ensure_slot(h, 1);
+    if (rc == SGM_OK && !h->h2d && cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    if (rc == SGM_OK && !h->d2h && cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    if (rc != SGM_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned long long t = h->tickets;
+    IoSlot &sl = h->io[t & 1];
+    const size_t npx = (size_t)h->W * h->H;
+    // inputs: once the slot's previous frame (t - 2) has been copied back
+    if (cudaStreamWaitEvent(h->h2d, sl.done, 0) != cudaSuccess ||
+        cudaMemcpyAsync(sl.left, left, npx, cudaMemcpyHostToDevice, h->h2d) != cudaSuccess ||
+        cudaMemcpyAsync(sl.right, right, npx, cudaMemcpyHostToDevice, h->h2d) != cudaSuccess ||
+        cudaEventRecord(sl.in_ready, h->h2d) != cudaSuccess)
+        return SGM_ERR_CUDA;
+    // the pipeline on the caller's stream, once the inputs are there
+    if (cudaStreamWaitEvent(s, sl.in_ready, 0) != cudaSuccess) return SGM_ERR_CUDA;
+    rc = compute_slot(h, sl, umap != nullptr, s);
+    if (rc != SGM_OK) return rc;
+    if (cudaEventRecord(sl.computed, s) != cudaSuccess) return SGM_ERR_CUDA;
+    // results: back to the host on the second copy stream
+    if (cudaStreamWaitEvent(h->d2h, sl.computed, 0) != cudaSuccess) return SGM_ERR_CUDA;
+    rc = copy_out(h, sl, disp, umap, vmap, h->d2h);
+    if (rc != SGM_OK) return rc;
+    if (cudaEventRecord(sl.done, h->d2h) != cudaSuccess) return SGM_ERR_CUDA;
+    *ticket = t;
+    h->tickets = t + 1;
+    return SGM_OK;
+}
+
+int sgm_host_wait(sgm_handle h, unsigned long long ticket) {
+    if (!h || ticket >= h->tickets) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    // the slot's done event was recorded by this frame or by a later one on
+    // the same copy stream; either way this frame's copies have finished
+    return cudaEventSynchronize(h->io[ticket & 1].done) == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
 
 int sgm_debug_census(sgm_handle h, const uint8_t *left, const uint8_t *right, uint64_t *codes_left,

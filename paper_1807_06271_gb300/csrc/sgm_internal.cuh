@@ -120,6 +120,15 @@ constexpr size_t kJobStateBytes = (size_t)(kJobClaimBase + kJobClaimSlots) * siz
 // increasing direction order), longest scanlines first; G = 32 / LPS.
 PathJobs make_path_jobs(int W, int H, int D, int mask);
 
+// Device staging of one frame for the host-pointer entry points.  done is
+// recorded after the frame's results have been copied back; in_ready after its
+// inputs have arrived; computed after its pipeline has run.
+struct IoSlot {
+    uint8_t *left, *right, *disp;
+    uint16_t *umap, *vmap;
+    cudaEvent_t in_ready, computed, done;
+};
+
 enum Stage { kStageCensus = 0, kStageCost, kStageAggregate, kStageWta, kStageMedian, kStageUv, kNumStages };
 
 struct TimingRecord {
@@ -150,9 +159,11 @@ struct sgm_handle_s {
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
     sgm::RectMaps rect;     // caller-owned rectification maps, or all null
 
-    // device staging for sgm_compute_host, allocated on first use
-    uint8_t *io_left, *io_right, *io_disp;
-    uint16_t *io_umap, *io_vmap;
+    // device staging of the host-pointer entry points, allocated on first use:
+    // slot 0 for sgm_compute_host, both slots in turn for sgm_compute_host_async
+    sgm::IoSlot io[2];
+    cudaStream_t h2d, d2h;       // copy streams of sgm_compute_host_async
+    unsigned long long tickets;  // frames submitted through sgm_compute_host_async
 
     // internal stream for sgm_batch_compute
     cudaStream_t side;

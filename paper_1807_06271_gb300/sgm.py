@@ -75,6 +75,8 @@ _SIGNATURES = {
     "sgm_compute": [_P, _P, _P, _P, _P],
     "uvmap_compute": [_P, _P, _P, _P, _P],
     "sgm_compute_host": [_P, _P, _P, _P, _P, _P, _P],
+    "sgm_compute_host_async": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "sgm_host_wait": [_P, ctypes.c_ulonglong],
     "sgm_batch_compute": [_I, _P, _P, _P, _P, _P, _P, _P],
     "sgm_get_shape": [_P, _P, _P, _P, _P],
     "sgm_debug_census": [_P, _P, _P, _P, _P, _P],
@@ -241,6 +243,22 @@ def sgm_compute_host(h: Handle, left, right, disp, umap=None, vmap=None, stream=
         h.ptr, _host(left, npx, "left"), _host(right, npx, "right"), _host(disp, npx, "disp"),
         _host(umap, 2 * h.D * h.W, "umap"), _host(vmap, 2 * h.H * h.D, "vmap"),
         _stream(stream)), "sgm_compute_host")
+
+
+def sgm_compute_host_async(h: Handle, left, right, disp, umap=None, vmap=None, stream=None) -> int:
+    """Queue one frame from host buffers (pinned); returns its ticket.  The
+    buffers belong to the frame until sgm_host_wait(h, ticket) returns."""
+    npx = h.W * h.H
+    t = ctypes.c_ulonglong()
+    _check(load().sgm_compute_host_async(
+        h.ptr, _host(left, npx, "left"), _host(right, npx, "right"), _host(disp, npx, "disp"),
+        _host(umap, 2 * h.D * h.W, "umap"), _host(vmap, 2 * h.H * h.D, "vmap"),
+        _stream(stream), ctypes.byref(t)), "sgm_compute_host_async")
+    return t.value
+
+
+def sgm_host_wait(h: Handle, ticket: int):
+    _check(load().sgm_host_wait(h.ptr, ctypes.c_ulonglong(ticket)), "sgm_host_wait")
 
 
 def sgm_batch_compute(handles, lefts, rights, disps, umaps=None, vmaps=None, stream=None):

@@ -80,6 +80,8 @@ def test_create_rejects_bad_arguments_on_host(W, H, D, kw, want):
 def test_null_arguments_are_rejected():
     lib = sgm.load()
     assert lib.sgm_create(10, 10, 16, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_host_wait(None, 0) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_compute_host_async(None, None, None, None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_compute(None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.uvmap_compute(None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_destroy(None) == sgm.SGM_ERR_INVALID_ARG

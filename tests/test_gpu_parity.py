@@ -230,6 +230,39 @@ def test_host_entry_point_matches_device_path():
             assert_same(V, o["V"], "V")
 
 
+def test_host_async_pipeline_matches_oracle_per_frame():
+    """Five different frames queued back to back through the two staging slots
+    (each slot reused), a synchronous call in between, then every frame
+    collected by its ticket."""
+    W, H, D = 160, 96, 48
+    p = params(5, 5, sgm.SGM_PATHS_8, 4, 24, 1, 3)
+    frames = [scenes.boxes_scene(W, H, D, seed=300 + i, n_boxes=3, dlo=2, dhi=D - 2) for i in range(5)]
+    want = [oracle.sgm(f.left, f.right, D, 5, 5, sgm.SGM_PATHS_8, 4, 24, 1, 3) for f in frames]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    ins = [(pin(f.left), pin(f.right)) for f in frames]
+    outs = [(torch.empty((H, W), dtype=torch.uint8).pin_memory(),
+             torch.empty((D, W), dtype=torch.int16).pin_memory(),
+             torch.empty((H, D), dtype=torch.int16).pin_memory()) for _ in frames]
+    with sgm.Handle(W, H, D, p) as h:
+        tickets = []
+        for i, ((l, r), (d, u, v)) in enumerate(zip(ins, outs)):
+            tickets.append(sgm.sgm_compute_host_async(h, l.numpy(), r.numpy(), d.numpy(),
+                                                       u.numpy().view(np.uint16), v.numpy().view(np.uint16)))
+            if i == 2:  # a synchronous frame between queued ones
+                d2 = np.empty((H, W), np.uint8)
+                sgm.sgm_compute_host(h, frames[0].left, frames[0].right, d2)
+                assert_same(d2, want[0]["disp"], "sync frame")
+        assert tickets == list(range(tickets[0], tickets[0] + 5))
+        for i, t in enumerate(tickets):
+            sgm.sgm_host_wait(h, t)
+            d, u, v = outs[i]
+            assert_same(d.numpy(), want[i]["disp"], f"disp {i}")
+            assert_same(u.numpy().view(np.uint16), want[i]["U"], f"U {i}")
+            assert_same(v.numpy().view(np.uint16), want[i]["V"], f"V {i}")
+        with pytest.raises(sgm.SgmError):
+            sgm.sgm_host_wait(h, tickets[-1] + 1)
+
+
 def test_batch_of_mixed_sizes_matches_oracle():
     specs = [(320, 240, 64), (160, 120, 32), (200, 90, 128), (64, 64, 16)]
     hs, Ls, Rs, Ds, Us, Vs, want = [], [], [], [], [], [], []

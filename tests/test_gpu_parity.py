@@ -115,6 +115,9 @@ CASES = [
     (150, 40, 128, 5, 5, 0xFF, 4, 24, 1, 3),
     (90, 30, 64, 5, 5, 0xFF, 2, 23, 1, 3),
     (90, 30, 64, 5, 5, 0xFF, 2, 24, 1, 3),
+    # widths that are not a multiple of a warp's pixel group, 64 disparities
+    (301, 9, 60, 5, 5, 0xFF, 4, 24, 1, 3),
+    (150, 12, 64, 9, 7, 0x0F, 8, 96, 2, 3),
 ]
 
 

@@ -19,11 +19,16 @@ namespace {
 constexpr int kBX = 32, kBY = 8;
 constexpr int kRows = 4;  // rows per thread of the unrolled census kernel
 
-// One CTA covers 32 x 32 pixels of one image; a thread computes 4 pixels of
-// one column.  The tile plus halo is staged as bytes with 255 for "outside
-// the image": 255 is never darker than a centre pixel, which gives the 0 bit
-// the border rule asks for.  Each bit is the sign of I(q) - I(p), shifted
-// into one of two 32-bit halves (two instructions per bit).
+// One CTA covers 32 x 32 pixels of one image; a thread computes the pixels
+// of kRows consecutive rows of one column.  The tile plus halo is staged as
+// bytes with 255 for "outside the image": 255 is never darker than a centre
+// pixel, which gives the 0 bit the border rule asks for.  Each bit is the
+// sign of I(q) - I(p), shifted into one of two 32-bit halves (two
+// instructions per bit).  The thread's windows overlap: it walks the
+// kRows + CH - 1 tile rows it touches from the bottom up, loads each row's CW
+// bytes once, and appends them to every pixel whose window holds that row;
+// every pixel thus receives its window backwards, so the first neighbour in
+// raster order ends at bit 0.
 template <typename CodeT, int CW, int CH, bool RECT>
 __global__ void __launch_bounds__(kBX *kBY)
     census_kernel(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch,
@@ -31,6 +36,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     wait_for_predecessor();
     constexpr int TW = kBX + CW - 1, TH = kBY * kRows + CH - 1;
     constexpr int RX = CW / 2, RY = CH / 2;
+    constexpr int NB = CW * CH - 1;  // bits per code
     __shared__ uint8_t tile[TH][TW];
     const uint8_t *img = blockIdx.z ? right : left;
     const uint16_t *mx = blockIdx.z ? maps.rx : maps.lx, *my = blockIdx.z ? maps.ry : maps.ly;
@@ -46,31 +52,42 @@ __global__ void __launch_bounds__(kBX *kBY)
     __syncthreads();
     const int x = blockIdx.x * kBX + threadIdx.x;
     if (x >= W) return;
+    const int ly0 = threadIdx.y * kRows;  // first tile row of the thread's windows
+    int c[kRows];
+    uint32_t lo[kRows], hi[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
-        const int ly = threadIdx.y + kBY * r;
-        const int y = blockIdx.y * kBY * kRows + ly;
-        if (y >= H) break;
-        const int c = tile[ly + RY][threadIdx.x + RX];
-        // I(q) - I(p) is negative exactly when q is darker; a funnel shift
-        // appends its sign bit.  Walking the window backwards leaves the
-        // first neighbour (raster order) at bit 0.
-        uint32_t lo = 0, hi = 0;
-        int bit = CW * CH - 2;
+        c[r] = tile[ly0 + r + RY][threadIdx.x + RX];
+        lo[r] = hi[r] = 0u;
+    }
 #pragma unroll
-        for (int wy = CH - 1; wy >= 0; wy--) {
+    for (int t = kRows + CH - 2; t >= 0; t--) {  // tile row ly0 + t, bottom up
+        int q[CW];
+#pragma unroll
+        for (int wx = 0; wx < CW; wx++) q[wx] = tile[ly0 + t][threadIdx.x + wx];
+#pragma unroll
+        for (int r = 0; r < kRows; r++) {
+            const int wy = t - r;  // window row of tile row t for pixel r
+            if (wy < 0 || wy >= CH) continue;
 #pragma unroll
             for (int wx = CW - 1; wx >= 0; wx--) {
                 if (wy == RY && wx == RX) continue;
-                const uint32_t diff = (uint32_t)((int)tile[ly + wy][threadIdx.x + wx] - c);
-                if (bit >= 32) hi = __funnelshift_l(diff, hi, 1);
-                else lo = __funnelshift_l(diff, lo, 1);
-                bit--;
+                // bit index of neighbour (wy, wx) in raster order, centre skipped
+                const int bit = wy * CW + wx - (wy * CW + wx > RY * CW + RX ? 1 : 0);
+                const uint32_t diff = (uint32_t)(q[wx] - c[r]);
+                if (bit >= 32) hi[r] = __funnelshift_l(diff, hi[r], 1);
+                else lo[r] = __funnelshift_l(diff, lo[r], 1);
             }
         }
+    }
+    static_assert(NB <= 64, "codes hold at most 64 bits");
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+        const int y = blockIdx.y * kBY * kRows + ly0 + r;
+        if (y >= H) break;
         CodeT code;
-        if constexpr (sizeof(CodeT) == 8) code = ((uint64_t)hi << 32) | lo;
-        else code = lo;
+        if constexpr (sizeof(CodeT) == 8) code = ((uint64_t)hi[r] << 32) | lo[r];
+        else code = lo[r];
         codes[(size_t)blockIdx.z * W * H + (size_t)y * W + x] = code;
     }
 }

@@ -6,7 +6,7 @@
 #include <mutex>
 #include <vector>
 
-#include "sgm_internal.cuh"
+#include "sgm_handle.cuh"
 
 namespace {
 

@@ -5,7 +5,7 @@
 
 #include <new>
 
-#include "sgm_internal.cuh"
+#include "sgm_handle.cuh"
 
 using namespace sgm;
 

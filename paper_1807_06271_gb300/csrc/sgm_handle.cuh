@@ -1,0 +1,77 @@
+// The handle of the C ABI and the host-side pieces shared by the entry points
+// (sgm_api.cu, batch.cu, and the map post-processing entry point in
+// uvpost.cu).  Kernel-only sources include sgm_internal.cuh alone.
+#pragma once
+
+#include "sgm_internal.cuh"
+
+namespace sgm {
+
+// Device staging of one frame for the host-pointer entry points.  done is
+// recorded after the frame's results have been copied back; in_ready after its
+// inputs have arrived; computed after its pipeline has run.
+struct IoSlot {
+    uint8_t *left, *right, *disp;
+    uint16_t *umap, *vmap;
+    cudaEvent_t in_ready, computed, done;
+};
+
+enum Stage { kStageCensus = 0, kStageCost, kStageAggregate, kStageWta, kStageMedian, kStageUv, kNumStages };
+
+struct TimingRecord {
+    int stage;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace sgm
+
+struct sgm_handle_s {
+    int W, H, D;
+    sgm_params p;
+    int nbits;       // largest matching cost: census bits, or window * 255 for SAD
+    int code_bytes;  // census: 4 (nbits <= 32) or 8; SAD: 0 (no codes)
+    int wide;        // 1: 16-bit costs and path costs (SAD), 0: 8-bit (census)
+    int device;
+    int npaths;
+    int path_of_plane[sgm::kMaxPaths];
+
+    int Dp;          // padded disparities per pixel (8 * lanes per scanline)
+
+    // scratch, owned
+    void *codes;        // [2][H][W] census codes (left, right); null for SAD
+    uint8_t *cost;      // [H][W][Dp] matching cost, lane-chunk order (bytes, or uint16 when wide)
+    uint8_t *planes;    // [H][W][npaths][Dp] per-path aggregated costs, same order
+    uint8_t *disp_lr;   // [H][W] after the LR check, before the median
+    unsigned *job_counter;  // work-queue state of the aggregation kernel (kJobStateBytes)
+    int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
+    sgm::RectMaps rect;     // caller-owned rectification maps, or all null
+
+    // device staging of the host-pointer entry points, allocated on first use:
+    // slot 0 for sgm_compute_host, both slots in turn for sgm_compute_host_async
+    sgm::IoSlot io[2];
+    cudaStream_t h2d, d2h;       // copy streams of sgm_compute_host_async
+    unsigned long long tickets;  // frames submitted through sgm_compute_host_async
+
+    // internal stream for sgm_batch_compute
+    cudaStream_t side;
+    cudaEvent_t fork_ev, join_ev;
+
+    // stage timing
+    int timing;
+    int rec_head, rec_count;
+    sgm::TimingRecord *recs;
+    double acc_ms[sgm::kNumStages];
+    int acc_n[sgm::kNumStages];
+};
+
+namespace sgm {
+
+// One pair (and its U/V maps when umap and vmap are non-null) on stream s.
+int compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
+                 uint16_t *umap, uint16_t *vmap, cudaStream_t s);
+// Drops cached batch graphs that use h (called before h is freed).
+void batch_forget(sgm_handle_s *h);
+// Aggregation blocks per SM chosen by sgm_autotune for h's shape, or 0.
+int tuned_blocks_per_sm(const sgm_handle_s *h);
+
+}  // namespace sgm

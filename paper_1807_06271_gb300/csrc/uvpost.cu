@@ -4,7 +4,7 @@
 // map tile plus a (r + 1)-cell halo is thresholded into shared memory, the
 // dilation is taken over a 1-cell halo, and the Gaussian over the tile.
 // Cells outside the map count as 0 in both filters.
-#include "sgm_internal.cuh"
+#include "sgm_handle.cuh"
 
 namespace sgm {
 namespace {

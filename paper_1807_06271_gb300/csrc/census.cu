@@ -42,12 +42,23 @@ __global__ void __launch_bounds__(kBX *kBY)
     const uint16_t *mx = blockIdx.z ? maps.rx : maps.lx, *my = blockIdx.z ? maps.ry : maps.ly;
     const int x0 = blockIdx.x * kBX - RX, y0 = blockIdx.y * kBY * kRows - RY;
     const int tid = threadIdx.y * kBX + threadIdx.x;
-    for (int i = tid; i < TW * TH; i += kBX * kBY) {
+    // All of a thread's tile loads are issued before any is stored, so their
+    // latencies overlap instead of adding up.
+    constexpr int kLoads = (TW * TH + kBX * kBY - 1) / (kBX * kBY);
+    uint8_t v[kLoads];
+#pragma unroll
+    for (int k = 0; k < kLoads; k++) {
+        const int i = tid + k * kBX * kBY;
         const int ty = i / TW, tx = i - ty * TW;
         const int gx = x0 + tx, gy = y0 + ty;
-        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H)
-                           ? rect_pixel<RECT>(img, pitch, W, H, gx, gy, mx, my)
-                           : 255;
+        v[k] = (i < TW * TH && gx >= 0 && gx < W && gy >= 0 && gy < H)
+                   ? rect_pixel<RECT>(img, pitch, W, H, gx, gy, mx, my)
+                   : 255;
+    }
+#pragma unroll
+    for (int k = 0; k < kLoads; k++) {
+        const int i = tid + k * kBX * kBY;
+        if (i < TW * TH) tile[i / TW][i % TW] = v[k];
     }
     __syncthreads();
     const int x = blockIdx.x * kBX + threadIdx.x;

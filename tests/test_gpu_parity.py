@@ -109,8 +109,9 @@ CASES = [
     (33, 17, 60, 5, 5, 0x55, 8, 32, 1, 5),
     (97, 61, 100, 9, 7, 0x3C, 7, 50, 1, 1),
     (45, 31, 2, 3, 5, 0x81, 1, 1, 0, 3),
-    # P2 on both sides of the code width (24 bits): the aggregation takes the
-    # running minimum from the previous step's costs only when P2 >= it
+    # P2 on both sides of the code width (24 bits): with P2 >= the largest
+    # cost the P2 term of Eq. 2 can never win over L(d*) + C for the previous
+    # minimum's disparity d*, below it it can
     (150, 40, 128, 5, 5, 0xFF, 4, 23, 1, 3),
     (150, 40, 128, 5, 5, 0xFF, 4, 24, 1, 3),
     (90, 30, 64, 5, 5, 0xFF, 2, 23, 1, 3),

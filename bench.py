@@ -474,6 +474,23 @@ def run_ours(args, w, windex):
     sgm.sgm_set_timing(h, False)
     sgm.sgm_set_rectification(h)
     extras["census_rectified_us"] = rect_stage["census"][0] / max(rect_stage["census"][1], 1) * 1e3
+    # the Hamming cost (Eq. 1) on each of its two kernels, same stage timing
+    if w.cost == 0 and 16 < w.D <= 128:
+        kernels = {}
+        for name, kern in (("cuda_cores", sgm.SGM_COST_KERNEL_CUDA_CORES),
+                           ("tensor_cores", sgm.SGM_COST_KERNEL_TENSOR_CORES)):
+            sgm.sgm_set_cost_kernel(h, kern)
+            for _ in range(3):
+                h.compute(left, right, disp, stream)
+            sgm.sgm_set_timing(h, True)
+            sgm.sgm_get_stage_times(h)
+            for _ in range(50):
+                h.compute(left, right, disp, stream)
+            st = sgm.sgm_get_stage_times(h)
+            sgm.sgm_set_timing(h, False)
+            kernels[name] = st["cost"][0] / max(st["cost"][1], 1) * 1e3
+        sgm.sgm_set_cost_kernel(h, sgm.SGM_COST_KERNEL_AUTO)
+        extras["cost_kernel_us"] = kernels
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -62,6 +62,16 @@ extern "C" {
                              images read with clamped (replicated) coordinates;
                              the paper pairs it with P1 = 200, P2 = 800         */
 
+/* Kernels for the Hamming costs of SGM_COST_CENSUS (Eq. 1); both give the
+ * same cost volume bit for bit.  With the census bits as entries +1 (bit
+ * clear) and -1 (bit set), the inner product of two codes is
+ * nbits - 2 * Hamming distance, so a row segment's costs are a band of a
+ * matrix product of the left and right codes. */
+#define SGM_COST_KERNEL_AUTO 0         /* the faster one on GB300: CUDA cores            */
+#define SGM_COST_KERNEL_CUDA_CORES 1   /* POPC of the XOR of the two codes, any D        */
+#define SGM_COST_KERNEL_TENSOR_CORES 2 /* the band on tcgen05 (e4m3 +-1 entries, f32
+                                          sums in tensor memory); 17 <= D <= 128    */
+
 typedef struct sgm_handle_s *sgm_handle;
 
 typedef struct sgm_params {
@@ -209,11 +219,29 @@ int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *righ
 int sgm_debug_sum(sgm_handle h, const uint8_t *left, const uint8_t *right,
                   uint16_t *S, void *stream);
 
+/* Matching cost C (Eq. 1, or the SAD of Sec. 3.1.2) computed by the given
+ * kernel (SGM_COST_KERNEL_*), H x W x D uint16 (device), d fastest; entries
+ * with x - d < 0 hold the largest cost (census bits, or window * 255).
+ * SGM_ERR_UNSUPPORTED when the kernel cannot serve the handle: tensor cores
+ * with D <= 16 or D > 128, or any kernel but AUTO on an SGM_COST_SAD handle. */
+int sgm_debug_cost(sgm_handle h, const uint8_t *left, const uint8_t *right, int kernel,
+                   uint16_t *C, void *stream);
+
 /* Left WTA, right WTA and the map after the LR check, before the median
  * (Sec. 3.1.3-3.1.4), H x W bytes each (device); any may be NULL. */
 int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right,
                   uint8_t *disp_left, uint8_t *disp_right, uint8_t *disp_lr,
                   void *stream);
+
+/* Cost kernel (SGM_COST_KERNEL_*) of later calls on h; AUTO when the handle
+ * is created.  SGM_ERR_UNSUPPORTED as for sgm_debug_cost (h unchanged). */
+int sgm_set_cost_kernel(sgm_handle h, int kernel);
+
+/* Waits for the device, then returns SGM_ERR_TIMEOUT if a kernel of h gave up
+ * a bounded device-side wait since the previous call (the tensor-core cost
+ * kernel waits about one second at most for its matrix product; it then
+ * writes no costs for that segment), else SGM_OK.  Clears the record. */
+int sgm_device_status(sgm_handle h);
 
 /* ---- stage timing (CUDA events on the caller's stream) ------------------- */
 

@@ -94,7 +94,7 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     } else {
         e = sgm::launch_census(left, right, pitch, W, H, params->census_w, params->census_h, code_bytes,
                                codes, no_maps, s);
-        if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, counter, s);
+        if (e == cudaSuccess) e = sgm::launch_cost(codes, code_bytes, W, H, D, nbits, cost, counter, nullptr, SGM_COST_KERNEL_AUTO, s);
     }
     if (e == cudaSuccess)
         e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, wide, jobs, planes, npaths,

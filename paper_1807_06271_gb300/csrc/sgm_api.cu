@@ -114,7 +114,8 @@ int run_cost(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cudaStr
         e = launch_sad_cost(left, right, pitch, h->W, h->H, h->D, h->p.census_w, h->p.census_h, h->rect,
                             reinterpret_cast<uint16_t *>(h->cost), h->job_counter, s);
     } else {
-        e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, h->job_counter, s);
+        e = launch_cost(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, h->job_counter, h->dev_status,
+                        h->cost_kernel, s);
     }
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
@@ -279,7 +280,11 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     const size_t eb = h->wide ? 2 : 1;  // bytes per cost / path cost
     rc = h->wide ? SGM_OK : dev_alloc(&h->codes, 2 * npx * h->code_bytes);
     if (rc == SGM_OK) rc = dev_alloc(&h->cost, npx * h->Dp * eb);
-    if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, kJobStateBytes);
+    if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, kJobStateBytes + sizeof(unsigned));
+    if (rc == SGM_OK) {
+        h->dev_status = h->job_counter + kJobStateBytes / sizeof(unsigned);
+        if (cudaMemset(h->dev_status, 0, sizeof(unsigned)) != cudaSuccess) rc = SGM_ERR_CUDA;
+    }
     if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * h->Dp * eb);
     if (rc == SGM_OK) rc = dev_alloc(&h->disp_lr, npx);
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
@@ -477,6 +482,51 @@ int sgm_debug_census(sgm_handle h, const uint8_t *left, const uint8_t *right, ui
             return SGM_ERR_CUDA;
     }
     return SGM_OK;
+}
+
+// SGM_OK when kernel (SGM_COST_KERNEL_*) can compute h's matching cost.
+static int check_cost_kernel(const sgm_handle_s *h, int kernel) {
+    if (kernel < SGM_COST_KERNEL_AUTO || kernel > SGM_COST_KERNEL_TENSOR_CORES) return SGM_ERR_INVALID_ARG;
+    if (h->wide && kernel != SGM_COST_KERNEL_AUTO) return SGM_ERR_UNSUPPORTED;
+    if (kernel == SGM_COST_KERNEL_TENSOR_CORES && !cost_mma_supported(h->D)) return SGM_ERR_UNSUPPORTED;
+    return SGM_OK;
+}
+
+int sgm_set_cost_kernel(sgm_handle h, int kernel) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    const int rc = check_cost_kernel(h, kernel);
+    if (rc == SGM_OK) h->cost_kernel = kernel;
+    return rc;
+}
+
+int sgm_device_status(sgm_handle h) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    unsigned v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&v, h->dev_status, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (v && cudaMemset(h->dev_status, 0, sizeof v) != cudaSuccess)) {
+        cudaGetLastError();
+        return SGM_ERR_CUDA;
+    }
+    return v ? SGM_ERR_TIMEOUT : SGM_OK;
+}
+
+int sgm_debug_cost(sgm_handle h, const uint8_t *left, const uint8_t *right, int kernel, uint16_t *C,
+                   void *stream) {
+    if (!h || !left || !right || !C) return SGM_ERR_INVALID_ARG;
+    int rc = check_cost_kernel(h, kernel);
+    if (rc != SGM_OK) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int keep = h->cost_kernel;
+    h->cost_kernel = kernel;
+    rc = run_matching(h, left, right, s);
+    h->cost_kernel = keep;
+    if (rc == SGM_OK && launch_unpermute(h->cost, h->W, h->H, h->D, h->wide != 0, C, s) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    return rc;
 }
 
 int sgm_debug_path(sgm_handle h, int r, const uint8_t *left, const uint8_t *right, uint16_t *L,

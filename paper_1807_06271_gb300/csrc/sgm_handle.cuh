@@ -42,7 +42,9 @@ struct sgm_handle_s {
     uint8_t *cost;      // [H][W][Dp] matching cost, lane-chunk order (bytes, or uint16 when wide)
     uint8_t *planes;    // [H][W][npaths][Dp] per-path aggregated costs, same order
     uint8_t *disp_lr;   // [H][W] after the LR check, before the median
-    unsigned *job_counter;  // work-queue state of the aggregation kernel (kJobStateBytes)
+    unsigned *job_counter;  // work-queue state of the aggregation kernel (kJobStateBytes), then dev_status
+    unsigned *dev_status;   // bit 0: a bounded device wait gave up (one word after the work-queue state)
+    int cost_kernel;        // SGM_COST_KERNEL_* of the census cost
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
     sgm::RectMaps rect;     // caller-owned rectification maps, or all null
 

@@ -130,8 +130,17 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
                           cudaStream_t s);
 // The cost kernels also clear job_state (kJobStateBytes, may be null), the
 // work-queue state of the aggregation kernel that follows them on the stream.
+// Hamming costs of the census codes come from one of two kernels (kernel:
+// SGM_COST_KERNEL_*): POPC on the CUDA cores (any D) or +-1 inner products on
+// the tensor cores (Dp <= 128), which ORs 1 into *status (may be null) when its
+// bounded wait for the MMA gives up.
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
-                        uint8_t *cost, unsigned *job_state, cudaStream_t s);
+                        uint8_t *cost, unsigned *job_state, unsigned *status, int kernel, cudaStream_t s);
+bool cost_mma_supported(int D);
+cudaError_t launch_cost_mma(const void *codes, int code_bytes, int W, int H, int D, int nbits, uint8_t *cost,
+                            unsigned *job_state, unsigned *status, cudaStream_t s);
+// The kernel SGM_COST_KERNEL_AUTO selects for D.
+int cost_kernel_for(int D);
 // SAD over a ww x wh window (clamped reads; rectified through maps when set) into a
 // 16-bit cost volume [H][W][Dp] in the wide lane-chunk order.
 cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,

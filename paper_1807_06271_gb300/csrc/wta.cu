@@ -6,7 +6,7 @@
 // disparities, DPL per lane, so a warp covers G = 32 / LPS neighbouring
 // pixels.  A lane loads its chunk of every plane (8 bytes of 8-bit path
 // costs, or 16 bytes of 16-bit ones) at fixed offsets from one pointer, one
-// pixel group ahead of its use (register double buffer), turns each into
+// or two pixel groups ahead of its use (register buffers), turns each into
 // DPL/2 packed 16-bit pairs (d+k, d+k+DPL/2) (masks and byte-permutes for
 // 8-bit planes; 16-bit planes are stored that way) and adds them.  No half
 // carries: S <= 8 * 255 for 8-bit planes, and the host bounds the 16-bit
@@ -152,8 +152,13 @@ __device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL, WIDE> (&v)[
     return best;
 }
 
-template <int LPS, int DPL, bool WIDE, int NP, bool RAGGED, bool DEBUG>
-__global__ void __launch_bounds__(kThreads)
+// PF: pixel groups whose planes are loaded ahead of the one being reduced (1
+// or 2).  The HBM read rate of this kernel rises with the bytes in flight:
+// two groups ahead took the 1242 x 375, D = 128 WTA from 87.5 to 81.4 us, but
+// the extra registers leave 3 instead of 4 CTAs per SM, so the launcher takes
+// PF = 2 only when that needs no more waves of rows.
+template <int LPS, int DPL, bool WIDE, int NP, bool RAGGED, bool DEBUG, int PF>
+__global__ void __launch_bounds__(kThreads, PF == 2 ? 2 : 1)
     wta_kernel(const uint8_t *__restrict__ planes, int nplanes, int W, int H,
                int D, int tol, uint8_t *__restrict__ disp_lr, uint8_t *__restrict__ dbg_left,
                uint8_t *__restrict__ dbg_right, uint16_t *__restrict__ dbg_sum) {
@@ -176,28 +181,36 @@ __global__ void __launch_bounds__(kThreads)
     const uint8_t *row = planes + (size_t)y * W * rec + DPL * EB * li;
     const uint64_t pol = policy_evict_first();
     const int stride = nwarps * G;
-    // software pipeline: the next pixel group's planes are loaded while the
-    // current one is reduced
-    PlaneChunk<DPL, WIDE> cur[kMaxPaths], nxt[kMaxPaths];
+    // software pipeline: the planes of the next PF pixel groups are loaded
+    // while the current one is reduced (buf[0] is the current group)
+    static_assert(PF == 1 || PF == 2, "one or two pixel groups ahead");
+    PlaneChunk<DPL, WIDE> buf[PF + 1][kMaxPaths];
     int x = warp * G + grp;
 #pragma unroll
-    for (int q = 0; q < kMaxPaths; q++)
+    for (int b = 0; b <= PF; b++)
 #pragma unroll
-        for (int w = 0; w < PlaneChunk<DPL, WIDE>::kWords; w++) cur[q].w[w] = nxt[q].w[w] = 0u;
+        for (int q = 0; q < kMaxPaths; q++)
 #pragma unroll
-    for (int q = 0; q < NQ; q++)
-        if ((NP > 0 || q < np) && x < W) cur[q] = ld_plane<DPL, WIDE>(row + (size_t)x * rec + q * Dp * EB, pol);
-    for (int xb = warp * G; xb < W; xb += stride) {
-        const int xn = x + stride;
+            for (int w = 0; w < PlaneChunk<DPL, WIDE>::kWords; w++) buf[b][q].w[w] = 0u;
+#pragma unroll
+    for (int b = 0; b < PF; b++)
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            if ((NP > 0 || q < np) && xn < W) nxt[q] = ld_plane<DPL, WIDE>(row + (size_t)xn * rec + q * Dp * EB, pol);
+            if ((NP > 0 || q < np) && x + b * stride < W)
+                buf[b][q] = ld_plane<DPL, WIDE>(row + (size_t)(x + b * stride) * rec + q * Dp * EB, pol);
+    for (int xb = warp * G; xb < W; xb += stride) {
+        const int xn = x + stride, xf = x + PF * stride;
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+            if ((NP > 0 || q < np) && xf < W) buf[PF][q] = ld_plane<DPL, WIDE>(row + (size_t)xf * rec + q * Dp * EB, pol);
         const bool active = x < W;
-        uint32_t best = pixel_keys<LPS, DPL, WIDE, NP, RAGGED, DEBUG>(cur, np, active, x, y, W, D, li, key_right, dbg_sum);
+        uint32_t best = pixel_keys<LPS, DPL, WIDE, NP, RAGGED, DEBUG>(buf[0], np, active, x, y, W, D, li, key_right, dbg_sum);
         best = group_min<LPS>(best, lane);
         if (li == 0 && active) dl_row[x] = (uint8_t)(best & 0xFFu);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) cur[q] = nxt[q];
+        for (int b = 0; b < PF; b++)
+#pragma unroll
+            for (int q = 0; q < NQ; q++) buf[b][q] = buf[b + 1][q];
         x = xn;
     }
     __syncthreads();
@@ -221,13 +234,35 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Launches one CTA per row of the PF = 2 variant when it needs no more waves
+// of rows than PF = 1 (resident CTAs per SM from the occupancy calculator).
+template <typename K1, typename K2>
+cudaError_t launch_rows(K1 k1, K2 k2, int H, size_t smem, cudaStream_t s, const uint8_t *planes, int nplanes, int W,
+                        int D, int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum) {
+    int dev = 0, sms = 0, n1 = 0, n2 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k1, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k2, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const long long c1 = (long long)n1 * sms, c2 = (long long)n2 * sms;
+    const bool deep = c2 > 0 && c1 > 0 && (H + c2 - 1) / c2 <= (H + c1 - 1) / c1;
+    if (deep)
+        return launch_k(k2, dim3(H), dim3(kThreads), smem, s, planes, nplanes, W, H, D, tol, disp_lr, dbg_left,
+                        dbg_right, dbg_sum);
+    return launch_k(k1, dim3(H), dim3(kThreads), smem, s, planes, nplanes, W, H, D, tol, disp_lr, dbg_left, dbg_right,
+                    dbg_sum);
+}
+
 template <bool WIDE>
 cudaError_t launch_wta_t(const uint8_t *planes, int nplanes, int W, int H, int D, int tol, uint8_t *disp_lr,
                          uint8_t *dbg_left, uint8_t *dbg_right, uint16_t *dbg_sum, size_t smem, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-#define SGM_WTA4(L, N, R, G)                                                                                    \
-    e = launch_k(wta_kernel<L, 8, WIDE, N, R, G>, dim3(H), dim3(kThreads), smem, s, planes, nplanes, W, H, D, tol, \
-                 disp_lr, dbg_left, dbg_right, dbg_sum)
+#define SGM_WTA4(L, N, R, G)                                                                                          \
+    e = (G) ? launch_k(wta_kernel<L, 8, WIDE, N, R, G, 1>, dim3(H), dim3(kThreads), smem, s, planes, nplanes, W, H, D, \
+                       tol, disp_lr, dbg_left, dbg_right, dbg_sum)                                                      \
+            : launch_rows(wta_kernel<L, 8, WIDE, N, R, G, 1>, wta_kernel<L, 8, WIDE, N, R, G, 2>, H, smem, s, planes, \
+                          nplanes, W, D, tol, disp_lr, dbg_left, dbg_right, dbg_sum)
 #define SGM_WTA(L)                                       \
     do {                                                 \
         const bool rag = D != 8 * (L);                   \

@@ -27,6 +27,11 @@ SGM_PATHS_STREAM4 = 0x55
 SGM_COST_CENSUS = 0  # Hamming distance of census codes over the window
 SGM_COST_SAD = 1  # sum of absolute differences over the window (16-bit path costs)
 
+# Kernels of the census Hamming cost (bit-identical results)
+SGM_COST_KERNEL_AUTO = 0  # the faster one on GB300 (CUDA cores)
+SGM_COST_KERNEL_CUDA_CORES = 1  # POPC of the XOR of two codes, any D
+SGM_COST_KERNEL_TENSOR_CORES = 2  # +-1 inner products on tcgen05 (17 <= D <= 128)
+
 STAGES = ("census", "cost", "aggregate", "wta_lr", "median", "uvmap")
 
 
@@ -89,6 +94,9 @@ _SIGNATURES = {
     "sgm_autotune": [_P, _P, _P, _P, _P, _P],
     "uvmap_postprocess": [_P, _P, _P, ctypes.POINTER(_UvPost), _P, _P, _P],
     "sgm_set_rectification": [_P, _P, _P, _P, _P],
+    "sgm_debug_cost": [_P, _P, _P, _I, _P, _P],
+    "sgm_set_cost_kernel": [_P, _I],
+    "sgm_device_status": [_P],
 }
 
 SGM_STATIC_SCRATCH_BYTES = 32 << 20
@@ -310,6 +318,23 @@ def sgm_debug_path(h: Handle, r: int, left, right, L, stream=None):
     _check(load().sgm_debug_path(
         h.ptr, r, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"),
         _dev(L, ("uint16", "int16"), (h.H, h.W, h.D), "L"), _stream(stream)), "sgm_debug_path")
+
+
+def sgm_debug_cost(h: Handle, left, right, C, kernel: int = SGM_COST_KERNEL_AUTO, stream=None):
+    """Matching cost C (H x W x D uint16) from the given cost kernel."""
+    shp = h._img_shape()
+    _check(load().sgm_debug_cost(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"), kernel,
+        _dev(C, ("uint16", "int16"), (h.H, h.W, h.D), "C"), _stream(stream)), "sgm_debug_cost")
+
+
+def sgm_set_cost_kernel(h: Handle, kernel: int):
+    _check(load().sgm_set_cost_kernel(h.ptr, kernel), "sgm_set_cost_kernel")
+
+
+def sgm_device_status(h: Handle) -> int:
+    """SGM_OK, or SGM_ERR_TIMEOUT if a bounded device wait of h gave up since the last call."""
+    return load().sgm_device_status(h.ptr)
 
 
 def sgm_debug_sum(h: Handle, left, right, S, stream=None):

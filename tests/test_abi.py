@@ -87,6 +87,9 @@ def test_null_arguments_are_rejected():
     assert lib.sgm_destroy(None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_batch_compute(-1, None, None, None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_batch_compute(0, None, None, None, None, None, None, None) == sgm.SGM_OK
+    assert lib.sgm_debug_cost(None, None, None, 0, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_set_cost_kernel(None, 0) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_device_status(None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_stage_name(0) == b"census"
     assert lib.sgm_stage_name(99) is None
 

@@ -415,6 +415,79 @@ def test_sad_stage_parity(case):
     compare_all(left, right, D, params(ww, wh, mask, P1, P2, tol, k, cost=sgm.SGM_COST_SAD))
 
 
+# Cost volumes of both Hamming-cost kernels: 128-pixel segments with ragged
+# last ones, every padded width Dp (8 .. 256), codes of 0 to 62 bits.
+COST_SHAPES = [
+    # W, H, D, cw, ch
+    (1242, 3, 128, 9, 7),
+    (1242, 40, 128, 9, 7),
+    (640, 100, 60, 5, 5),
+    (300, 4, 60, 5, 5),
+    (129, 5, 100, 9, 7),
+    (128, 2, 64, 7, 9),
+    (257, 3, 33, 5, 5),
+    (40, 6, 16, 3, 3),
+    (5, 4, 8, 1, 1),
+    (77, 3, 1, 5, 3),
+    (1, 7, 3, 5, 5),
+    (3, 2, 17, 5, 5),
+    (200, 3, 129, 9, 7),
+    (90, 2, 255, 5, 5),
+]
+
+
+@pytest.mark.parametrize("case", COST_SHAPES, ids=lambda c: "x".join(map(str, c)))
+def test_cost_volume_of_each_kernel_matches_oracle(case):
+    W, H, D, cw, ch = case
+    r = np.random.default_rng(W * 7 + D)
+    left = r.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.roll(left, min(D - 1, 9), axis=1) ^ (r.random((H, W)) < 0.2).astype(np.uint8) * 29
+    nbits = cw * ch - 1
+    want = oracle.cost_volume(oracle.census(left, cw, ch), oracle.census(right, cw, ch), D, nbits)
+    with sgm.Handle(W, H, D, params(cw, ch, 0x0F, 1, 255 - nbits, 1, 0)) as h:
+        L, R = cuda(left), cuda(right)
+        for kernel in (sgm.SGM_COST_KERNEL_AUTO, sgm.SGM_COST_KERNEL_CUDA_CORES, sgm.SGM_COST_KERNEL_TENSOR_CORES):
+            C = torch.full((H, W, D), -1, dtype=torch.int16, device="cuda")
+            if kernel == sgm.SGM_COST_KERNEL_TENSOR_CORES and not 16 < D <= 128:
+                with pytest.raises(sgm.SgmError) as e:
+                    sgm.sgm_debug_cost(h, L, R, C, kernel)
+                assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
+                continue
+            sgm.sgm_debug_cost(h, L, R, C, kernel)
+            torch.cuda.synchronize()
+            assert_same(u16(C), want, f"cost volume, kernel {kernel}")
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK
+
+
+@pytest.mark.parametrize("kernel", [sgm.SGM_COST_KERNEL_CUDA_CORES, sgm.SGM_COST_KERNEL_TENSOR_CORES])
+def test_pipeline_with_each_cost_kernel(kernel):
+    s = scenes.boxes_scene(300, 60, 128, seed=11, n_boxes=4, dlo=4, dhi=120)
+    p = params(9, 7, 0xFF, 8, 96, 1, 3)
+    o = oracle.sgm(s.left, s.right, 128, 9, 7, 0xFF, 8, 96, 1, 3, uv=False)["disp"]
+    with sgm.Handle(300, 60, 128, p) as h:
+        sgm.sgm_set_cost_kernel(h, kernel)
+        disp = torch.empty((60, 300), dtype=torch.uint8, device="cuda")
+        h.compute(cuda(s.left), cuda(s.right), disp)
+        torch.cuda.synchronize()
+        assert_same(disp.cpu().numpy(), o, "disparity")
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK
+
+
+def test_cost_kernel_choice_is_checked():
+    with sgm.Handle(64, 8, 200, params(5, 5, 0x0F, 4, 24, 1, 3)) as h:
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_set_cost_kernel(h, sgm.SGM_COST_KERNEL_TENSOR_CORES)
+        assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_set_cost_kernel(h, 7)
+        assert e.value.status == sgm.SGM_ERR_INVALID_ARG
+    with sgm.Handle(16, 8, 8, params(5, 5, 0x0F, 200, 800, 1, 3, cost=sgm.SGM_COST_SAD)) as h:
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_set_cost_kernel(h, sgm.SGM_COST_KERNEL_CUDA_CORES)
+        assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
+        sgm.sgm_set_cost_kernel(h, sgm.SGM_COST_KERNEL_AUTO)
+
+
 def test_sad_handle_has_no_census_codes():
     p = params(5, 5, 0x0F, 200, 800, 1, 3, cost=sgm.SGM_COST_SAD)
     with sgm.Handle(16, 8, 8, p) as h:

@@ -39,6 +39,7 @@ extern "C" {
 #define SGM_ERR_OOM 3         /* device or pinned-host allocation failed          */
 #define SGM_ERR_CUDA 4        /* a CUDA runtime call or kernel launch failed      */
 #define SGM_ERR_TIMEOUT 5     /* a bounded device-side wait gave up               */
+#define SGM_ERR_OVERRUN 6     /* a guard byte next to a buffer changed (canaries) */
 
 #define SGM_INVALID 0xFF
 
@@ -242,6 +243,36 @@ int sgm_set_cost_kernel(sgm_handle h, int kernel);
  * kernel waits about one second at most for its matrix product; it then
  * writes no costs for that segment), else SGM_OK.  Clears the record. */
 int sgm_device_status(sgm_handle h);
+
+/* Test of the bounded device waits: runs the census and the tensor-core cost
+ * kernel in a mode whose first wait is on an mbarrier that nothing arrives
+ * at, so it gives up after 2 ms and records the timeout.  The matrix
+ * products still complete and the handle stays usable; the cost volume of
+ * this call is not valid.  A following sgm_device_status(h) returns
+ * SGM_ERR_TIMEOUT.  SGM_ERR_UNSUPPORTED where the tensor-core kernel cannot
+ * serve the handle (see sgm_debug_cost). */
+int sgm_debug_stalled_wait(sgm_handle h, const uint8_t *left, const uint8_t *right, void *stream);
+
+/* ---- fault-detection hooks (tests) ---------------------------------------- */
+
+/* Process-wide: the n-th device allocation the library makes from now on
+ * fails as if the device were out of memory (n = 0: none).  The call that
+ * hits it returns SGM_ERR_OOM and releases what it had allocated. */
+int sgm_debug_fail_alloc(int n);
+
+/* Process-wide: handles created while on (1) place 256 guard bytes of 0xA5
+ * before and after each of their device buffers (scratch and staging). */
+int sgm_debug_canaries(int on);
+
+/* Waits for the device, then checks every guard byte of h: SGM_OK, or
+ * SGM_ERR_OVERRUN if one changed (a kernel wrote outside its buffer).
+ * SGM_ERR_UNSUPPORTED for a handle created without canaries. */
+int sgm_debug_check_canaries(sgm_handle h);
+
+/* Changes the first guard byte after device buffer i of h (in allocation
+ * order), from the host: the test of sgm_debug_check_canaries itself.
+ * SGM_ERR_UNSUPPORTED without canaries, SGM_ERR_INVALID_ARG for a bad i. */
+int sgm_debug_poke_canary(sgm_handle h, int i);
 
 /* ---- stage timing (CUDA events on the caller's stream) ------------------- */
 

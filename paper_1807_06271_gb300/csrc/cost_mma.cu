@@ -55,7 +55,10 @@
 // Waits.  The waits are on the mbarriers that MMA completion arrives on; each
 // gives up after about one second.  The CTA then records the timeout in
 // *status, waits once more for its MMAs and copies in flight, frees its
-// tensor memory and stops (segments it had not finished keep old costs).
+// tensor memory and stops (segments it had not finished keep old costs).  A
+// test mode (stall_test) points the first wait at a third mbarrier that
+// nothing arrives at, with a 2 ms limit, so the whole timeout path runs
+// without any fault: the MMAs still complete, and the handle stays usable.
 #include "sgm_internal.cuh"
 
 namespace sgm {
@@ -73,6 +76,7 @@ constexpr int kBarOperands = 1, kBarCost = 2;
 __device__ __forceinline__ int operand_bar(int k) { return kBarOperands + 2 * (k & 1); }
 constexpr uint32_t kTmemCols = 512;  // two accumulator buffers of 256 columns
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+constexpr unsigned long long kStallTestLimitNs = 2000000ull;  // the stalled-wait test gives up after 2 ms
 constexpr int kOneCtaPerSm = 116 * 1024;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -148,8 +152,8 @@ __device__ __forceinline__ bool bar_or(int id, int count, bool v) {
     return r != 0;
 }
 
-// Waits for the phase of parity `parity` of the mbarrier at bar, giving up after kWaitLimitNs.
-__device__ __forceinline__ bool wait_mbar(uint32_t bar, uint32_t parity) {
+// Waits for the phase of parity `parity` of the mbarrier at bar, giving up after limit_ns.
+__device__ __forceinline__ bool wait_mbar(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kWaitLimitNs) {
     const unsigned long long t0 = global_ns();
     for (;;) {
         uint32_t done;
@@ -159,7 +163,7 @@ __device__ __forceinline__ bool wait_mbar(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -173,8 +177,8 @@ struct Smem {
     static constexpr int kT = 5 * kOp;            // cost bytes, [128] rows
     static constexpr int kTPitch = LC + 8;        // odd number of 8-byte units: conflict-free row stores
     static constexpr int kO = kT + kM * kTPitch;  // staged records [2][128][DP]
-    static constexpr int kBar = kO + 2 * kM * DP; // two mbarriers
-    static constexpr int kSlot = kBar + 16;      // TMEM address, then the abort flag
+    static constexpr int kBar = kO + 2 * kM * DP; // two mbarriers, then one nothing arrives at
+    static constexpr int kSlot = kBar + 32;      // TMEM address, then the abort flag
     static constexpr int kBytes = kSlot + 16;
     static_assert(kT % 16 == 0 && kO % 16 == 0 && kBar % 16 == 0, "16-byte aligned regions");
 };
@@ -183,7 +187,7 @@ template <int DP, int KB, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, 1)
     hamming_mma_kernel(const uint32_t *__restrict__ codes, int W, int H, int D, int nbits,
                        uint8_t *__restrict__ cost, unsigned *__restrict__ job_state,
-                       unsigned *__restrict__ status) {
+                       unsigned *__restrict__ status, int stall_test) {
     using L = Smem<DP, KB>;
     constexpr int LC = L::LC, NCH = DP / 8, CPP = NCH / 4;  // chunks per thread in the record step
     constexpr int CW = KB / 32;                             // 32-bit words per code
@@ -210,6 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 16) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
 
@@ -315,7 +320,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             bar_arrive(operand_bar(k + 1), kThreads);  // operands of k+1 staged, TMEM buffer (k+1) & 1 free
         }
-        if (bar_or(kBarCost, kCostThreads, !wait_mbar(bar0 + 8u * (uint32_t)(k & 1), (uint32_t)(k >> 1) & 1u))) {
+        // stall_test: the first wait is on the barrier nothing arrives at, so it runs out (tests the timeout path)
+        const bool ok = stall_test && k == 0 ? wait_mbar(bar0 + 16u, 0u, kStallTestLimitNs)
+                                             : wait_mbar(bar0 + 8u * (uint32_t)(k & 1), (uint32_t)(k >> 1) & 1u);
+        if (bar_or(kBarCost, kCostThreads, !ok)) {
             if (tid == 0) {
                 if (status) atomicOr(status, 1u);
                 *abort_flag = 1;
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int DP, int KB, bool RAGGED>
 cudaError_t launch_dp(const void *codes, int W, int H, int D, int nbits, uint8_t *cost, unsigned *job_state,
-                      unsigned *status, cudaStream_t s) {
+                      unsigned *status, int stall_test, cudaStream_t s) {
     auto kernel = hamming_mma_kernel<DP, KB, RAGGED>;
     // More than half an SM's shared memory: two CTAs never share an SM (the
     // second would wait in tcgen05.alloc until the first had finished).
@@ -437,17 +445,17 @@ cudaError_t launch_dp(const void *codes, int W, int H, int D, int nbits, uint8_t
     const long long nseg = (long long)((W + kM - 1) / kM) * H;
     const int grid = nseg < sms ? (int)nseg : sms;
     return launch_k(kernel, dim3(grid), dim3(kThreads), (size_t)smem, s, (const uint32_t *)codes, W, H, D, nbits,
-                    cost, job_state, status);
+                    cost, job_state, status, stall_test);
 }
 
 template <int KB>
 cudaError_t launch_kb(const void *codes, int W, int H, int D, int nbits, uint8_t *cost, unsigned *job_state,
-                      unsigned *status, cudaStream_t s) {
+                      unsigned *status, int stall_test, cudaStream_t s) {
     const int Dp = padded_disparities(D);
     const bool rag = D != Dp;
 #define SGM_MMA(P)                                                                                 \
-    return rag ? launch_dp<P, KB, true>(codes, W, H, D, nbits, cost, job_state, status, s)        \
-               : launch_dp<P, KB, false>(codes, W, H, D, nbits, cost, job_state, status, s)
+    return rag ? launch_dp<P, KB, true>(codes, W, H, D, nbits, cost, job_state, status, stall_test, s) \
+               : launch_dp<P, KB, false>(codes, W, H, D, nbits, cost, job_state, status, stall_test, s)
     switch (Dp) {
         case 32: SGM_MMA(32);
         case 64: SGM_MMA(64);
@@ -465,11 +473,11 @@ bool cost_mma_supported(int D) {
 }
 
 cudaError_t launch_cost_mma(const void *codes, int code_bytes, int W, int H, int D, int nbits, uint8_t *cost,
-                            unsigned *job_state, unsigned *status, cudaStream_t s) {
+                            unsigned *job_state, unsigned *status, cudaStream_t s, int stall_test) {
     if (!cost_mma_supported(D) || nbits < 0 || nbits > 8 * code_bytes) return cudaErrorInvalidValue;
     if (W <= 0 || H <= 0) return cudaSuccess;
-    if (code_bytes == 4) return launch_kb<32>(codes, W, H, D, nbits, cost, job_state, status, s);
-    if (code_bytes == 8) return launch_kb<64>(codes, W, H, D, nbits, cost, job_state, status, s);
+    if (code_bytes == 4) return launch_kb<32>(codes, W, H, D, nbits, cost, job_state, status, stall_test, s);
+    if (code_bytes == 8) return launch_kb<64>(codes, W, H, D, nbits, cost, job_state, status, stall_test, s);
     return cudaErrorInvalidValue;
 }
 

@@ -3,7 +3,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
+#include <vector>
 
 #include "sgm_handle.cuh"
 
@@ -176,17 +178,8 @@ int uv_on(sgm_handle_s *h, const uint8_t *disp, uint16_t *umap, uint16_t *vmap, 
 
 void free_handle(sgm_handle_s *h) {
     if (!h) return;
-    cudaFree(h->codes);
-    cudaFree(h->cost);
-    cudaFree(h->job_counter);
-    cudaFree(h->planes);
-    cudaFree(h->disp_lr);
+    for (int i = 0; i < h->nallocs; i++) cudaFree(h->allocs[i].base);
     for (IoSlot &sl : h->io) {
-        cudaFree(sl.left);
-        cudaFree(sl.right);
-        cudaFree(sl.disp);
-        cudaFree(sl.umap);
-        cudaFree(sl.vmap);
         if (sl.in_ready) cudaEventDestroy(sl.in_ready);
         if (sl.computed) cudaEventDestroy(sl.computed);
         if (sl.done) cudaEventDestroy(sl.done);
@@ -206,15 +199,40 @@ void free_handle(sgm_handle_s *h) {
     free(h);
 }
 
+// Test hooks (process-wide): the n-th device allocation from now fails
+// (sgm_debug_fail_alloc), and handles created while canaries are on guard
+// their allocations (sgm_debug_canaries).
+std::atomic<int> g_fail_alloc_in{0};
+std::atomic<int> g_canaries{0};
+
+// A device buffer of `bytes` for handle h, recorded in h->allocs.
 template <typename T>
-int dev_alloc(T **p, size_t bytes) {
+int dev_alloc(sgm_handle_s *h, T **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 1;
-    cudaError_t e = cudaMalloc((void **)p, bytes);
-    if (e == cudaSuccess) return SGM_OK;
-    cudaGetLastError();
-    *p = nullptr;
-    return e == cudaErrorMemoryAllocation ? SGM_ERR_OOM : SGM_ERR_CUDA;
+    if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) return SGM_ERR_OOM;
+    if (h->nallocs == kMaxAllocs) return SGM_ERR_CUDA;
+    const size_t pad = h->canaries ? kCanaryBytes : 0;
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes + 2 * pad);
+    if (e == cudaSuccess && pad &&
+        (cudaMemset(base, kCanaryByte, pad) != cudaSuccess ||
+         cudaMemset((unsigned char *)base + pad + bytes, kCanaryByte, pad) != cudaSuccess)) {
+        cudaFree(base);
+        e = cudaErrorUnknown;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SGM_ERR_OOM : SGM_ERR_CUDA;
+    }
+    h->allocs[h->nallocs++] = DevAlloc{base, bytes};
+    *p = reinterpret_cast<T *>((unsigned char *)base + pad);
+    return SGM_OK;
+}
+
+// Frees the allocations made after the first `keep` (a failed multi-buffer setup).
+void dev_release_after(sgm_handle_s *h, int keep) {
+    while (h->nallocs > keep) cudaFree(h->allocs[--h->nallocs].base);
 }
 
 }  // namespace
@@ -241,6 +259,7 @@ const char *sgm_status_string(int status) {
         case SGM_ERR_OOM: return "out of memory";
         case SGM_ERR_CUDA: return "CUDA error";
         case SGM_ERR_TIMEOUT: return "device wait timed out";
+        case SGM_ERR_OVERRUN: return "a kernel wrote outside its buffer";
         default: return "unknown status";
     }
 }
@@ -278,15 +297,16 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     }
     const size_t npx = (size_t)W * H;
     const size_t eb = h->wide ? 2 : 1;  // bytes per cost / path cost
-    rc = h->wide ? SGM_OK : dev_alloc(&h->codes, 2 * npx * h->code_bytes);
-    if (rc == SGM_OK) rc = dev_alloc(&h->cost, npx * h->Dp * eb);
-    if (rc == SGM_OK) rc = dev_alloc(&h->job_counter, kJobStateBytes + sizeof(unsigned));
+    h->canaries = g_canaries.load();
+    rc = h->wide ? SGM_OK : dev_alloc(h, &h->codes, 2 * npx * h->code_bytes);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->cost, npx * h->Dp * eb);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->job_counter, kJobStateBytes + sizeof(unsigned));
     if (rc == SGM_OK) {
         h->dev_status = h->job_counter + kJobStateBytes / sizeof(unsigned);
         if (cudaMemset(h->dev_status, 0, sizeof(unsigned)) != cudaSuccess) rc = SGM_ERR_CUDA;
     }
-    if (rc == SGM_OK) rc = dev_alloc(&h->planes, (size_t)h->npaths * npx * h->Dp * eb);
-    if (rc == SGM_OK) rc = dev_alloc(&h->disp_lr, npx);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->planes, (size_t)h->npaths * npx * h->Dp * eb);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->disp_lr, npx);
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
         rc = SGM_ERR_CUDA;
     if (rc == SGM_OK && (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -341,21 +361,18 @@ int ensure_slot(sgm_handle_s *h, int i) {
     IoSlot &sl = h->io[i];
     if (sl.left) return SGM_OK;
     const size_t npx = (size_t)h->W * h->H;
-    int rc = dev_alloc(&sl.left, npx);
-    if (rc == SGM_OK) rc = dev_alloc(&sl.right, npx);
-    if (rc == SGM_OK) rc = dev_alloc(&sl.disp, npx);
-    if (rc == SGM_OK) rc = dev_alloc(&sl.umap, (size_t)h->D * h->W * sizeof(uint16_t));
-    if (rc == SGM_OK) rc = dev_alloc(&sl.vmap, (size_t)h->H * h->D * sizeof(uint16_t));
+    const int keep = h->nallocs;
+    int rc = dev_alloc(h, &sl.left, npx);
+    if (rc == SGM_OK) rc = dev_alloc(h, &sl.right, npx);
+    if (rc == SGM_OK) rc = dev_alloc(h, &sl.disp, npx);
+    if (rc == SGM_OK) rc = dev_alloc(h, &sl.umap, (size_t)h->D * h->W * sizeof(uint16_t));
+    if (rc == SGM_OK) rc = dev_alloc(h, &sl.vmap, (size_t)h->H * h->D * sizeof(uint16_t));
     if (rc == SGM_OK && (cudaEventCreateWithFlags(&sl.in_ready, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess))
         rc = SGM_ERR_CUDA;
     if (rc != SGM_OK) {
-        cudaFree(sl.left);
-        cudaFree(sl.right);
-        cudaFree(sl.disp);
-        cudaFree(sl.umap);
-        cudaFree(sl.vmap);
+        dev_release_after(h, keep);
         if (sl.in_ready) cudaEventDestroy(sl.in_ready);
         if (sl.computed) cudaEventDestroy(sl.computed);
         if (sl.done) cudaEventDestroy(sl.done);
@@ -512,6 +529,55 @@ int sgm_device_status(sgm_handle h) {
     return v ? SGM_ERR_TIMEOUT : SGM_OK;
 }
 
+int sgm_debug_fail_alloc(int n) {
+    if (n < 0) return SGM_ERR_INVALID_ARG;
+    g_fail_alloc_in.store(n);
+    return SGM_OK;
+}
+
+int sgm_debug_canaries(int on) {
+    g_canaries.store(on ? 1 : 0);
+    return SGM_OK;
+}
+
+int sgm_debug_check_canaries(sgm_handle h) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    if (!h->canaries) return SGM_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return SGM_ERR_CUDA;
+    }
+    std::vector<unsigned char> pad(kCanaryBytes);
+    for (int i = 0; i < h->nallocs; i++) {
+        const unsigned char *b = (const unsigned char *)h->allocs[i].base;
+        for (const unsigned char *src : {b, b + kCanaryBytes + h->allocs[i].bytes}) {
+            if (cudaMemcpy(pad.data(), src, kCanaryBytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaGetLastError();
+                return SGM_ERR_CUDA;
+            }
+            for (unsigned char c : pad)
+                if (c != kCanaryByte) return SGM_ERR_OVERRUN;
+        }
+    }
+    return SGM_OK;
+}
+
+int sgm_debug_poke_canary(sgm_handle h, int i) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    if (!h->canaries) return SGM_ERR_UNSUPPORTED;
+    if (i < 0 || i >= h->nallocs) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    unsigned char *after = (unsigned char *)h->allocs[i].base + kCanaryBytes + h->allocs[i].bytes;
+    if (cudaMemset(after, (unsigned char)~kCanaryByte, 1) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return SGM_ERR_CUDA;
+    }
+    return SGM_OK;
+}
+
 int sgm_debug_cost(sgm_handle h, const uint8_t *left, const uint8_t *right, int kernel, uint16_t *C,
                    void *stream) {
     if (!h || !left || !right || !C) return SGM_ERR_INVALID_ARG;
@@ -525,6 +591,20 @@ int sgm_debug_cost(sgm_handle h, const uint8_t *left, const uint8_t *right, int 
     rc = run_matching(h, left, right, s);
     h->cost_kernel = keep;
     if (rc == SGM_OK && launch_unpermute(h->cost, h->W, h->H, h->D, h->wide != 0, C, s) != cudaSuccess)
+        rc = SGM_ERR_CUDA;
+    return rc;
+}
+
+int sgm_debug_stalled_wait(sgm_handle h, const uint8_t *left, const uint8_t *right, void *stream) {
+    if (!h || !left || !right) return SGM_ERR_INVALID_ARG;
+    int rc = check_cost_kernel(h, SGM_COST_KERNEL_TENSOR_CORES);
+    if (rc != SGM_OK) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = run_census(h, left, right, s);
+    if (rc == SGM_OK && launch_cost_mma(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->cost, h->job_counter,
+                                        h->dev_status, s, 1) != cudaSuccess)
         rc = SGM_ERR_CUDA;
     return rc;
 }

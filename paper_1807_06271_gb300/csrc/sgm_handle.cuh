@@ -23,6 +23,17 @@ struct TimingRecord {
     cudaEvent_t start, stop;
 };
 
+// One device allocation of a handle.  With canaries on, kCanaryBytes of
+// kCanaryByte sit before and after the bytes the handle uses (base is the
+// cudaMalloc pointer; the handle's pointer is base + kCanaryBytes).
+struct DevAlloc {
+    void *base;
+    size_t bytes;
+};
+constexpr int kMaxAllocs = 16;
+constexpr size_t kCanaryBytes = 256;  // keeps the buffers 256-byte aligned
+constexpr unsigned char kCanaryByte = 0xA5;
+
 }  // namespace sgm
 
 struct sgm_handle_s {
@@ -36,6 +47,11 @@ struct sgm_handle_s {
     int path_of_plane[sgm::kMaxPaths];
 
     int Dp;          // padded disparities per pixel (8 * lanes per scanline)
+
+    // every device allocation of the handle (scratch and staging), freed by sgm_destroy
+    sgm::DevAlloc allocs[sgm::kMaxAllocs];
+    int nallocs;
+    int canaries;  // allocations carry guard bytes on both sides (sgm_debug_canaries)
 
     // scratch, owned
     void *codes;        // [2][H][W] census codes (left, right); null for SAD

@@ -137,8 +137,10 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
 cudaError_t launch_cost(const void *codes, int code_bytes, int W, int H, int D, int nbits,
                         uint8_t *cost, unsigned *job_state, unsigned *status, int kernel, cudaStream_t s);
 bool cost_mma_supported(int D);
+// stall_test != 0: the kernel's first wait is on an mbarrier nothing arrives at,
+// with a 2 ms limit, so that it takes its timeout path (for tests of it).
 cudaError_t launch_cost_mma(const void *codes, int code_bytes, int W, int H, int D, int nbits, uint8_t *cost,
-                            unsigned *job_state, unsigned *status, cudaStream_t s);
+                            unsigned *job_state, unsigned *status, cudaStream_t s, int stall_test = 0);
 // The kernel SGM_COST_KERNEL_AUTO selects for D.
 int cost_kernel_for(int D);
 // SAD over a ww x wh window (clamped reads; rectified through maps when set) into a

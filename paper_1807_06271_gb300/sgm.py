@@ -19,6 +19,7 @@ SGM_ERR_UNSUPPORTED = 2
 SGM_ERR_OOM = 3
 SGM_ERR_CUDA = 4
 SGM_ERR_TIMEOUT = 5
+SGM_ERR_OVERRUN = 6
 SGM_INVALID = 0xFF
 
 SGM_PATHS_4 = 0x0F
@@ -97,6 +98,11 @@ _SIGNATURES = {
     "sgm_debug_cost": [_P, _P, _P, _I, _P, _P],
     "sgm_set_cost_kernel": [_P, _I],
     "sgm_device_status": [_P],
+    "sgm_debug_stalled_wait": [_P, _P, _P, _P],
+    "sgm_debug_fail_alloc": [_I],
+    "sgm_debug_canaries": [_I],
+    "sgm_debug_check_canaries": [_P],
+    "sgm_debug_poke_canary": [_P, _I],
 }
 
 SGM_STATIC_SCRATCH_BYTES = 32 << 20
@@ -335,6 +341,33 @@ def sgm_set_cost_kernel(h: Handle, kernel: int):
 def sgm_device_status(h: Handle) -> int:
     """SGM_OK, or SGM_ERR_TIMEOUT if a bounded device wait of h gave up since the last call."""
     return load().sgm_device_status(h.ptr)
+
+
+def sgm_debug_stalled_wait(h: Handle, left, right, stream=None):
+    """Runs the tensor-core cost kernel with a wait that runs out (see sgm.h)."""
+    shp = h._img_shape()
+    _check(load().sgm_debug_stalled_wait(
+        h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"), _stream(stream)),
+        "sgm_debug_stalled_wait")
+
+
+def sgm_debug_fail_alloc(n: int):
+    """The n-th device allocation of the library from now on fails (0: none)."""
+    _check(load().sgm_debug_fail_alloc(n), "sgm_debug_fail_alloc")
+
+
+def sgm_debug_canaries(on: bool):
+    """Handles created while on guard their device buffers with canary bytes."""
+    _check(load().sgm_debug_canaries(1 if on else 0), "sgm_debug_canaries")
+
+
+def sgm_debug_check_canaries(h: Handle) -> int:
+    """SGM_OK, or SGM_ERR_OVERRUN if a guard byte of h changed."""
+    return load().sgm_debug_check_canaries(h.ptr)
+
+
+def sgm_debug_poke_canary(h: Handle, i: int):
+    _check(load().sgm_debug_poke_canary(h.ptr, i), "sgm_debug_poke_canary")
 
 
 def sgm_debug_sum(h: Handle, left, right, S, stream=None):

@@ -90,6 +90,7 @@ def test_null_arguments_are_rejected():
     assert lib.sgm_debug_cost(None, None, None, 0, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_set_cost_kernel(None, 0) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_device_status(None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_debug_stalled_wait(None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_stage_name(0) == b"census"
     assert lib.sgm_stage_name(99) is None
 

@@ -473,6 +473,33 @@ def test_pipeline_with_each_cost_kernel(kernel):
         assert sgm.sgm_device_status(h) == sgm.SGM_OK
 
 
+def test_bounded_wait_reports_timeout_and_handle_recovers():
+    """The tensor-core cost kernel's first wait runs out on an mbarrier nothing
+    arrives at: the call records SGM_ERR_TIMEOUT, the matrix products still
+    drain, and the next frame on the same handle is bit-exact again."""
+    s = scenes.boxes_scene(700, 40, 128, seed=5, n_boxes=3, dlo=4, dhi=120)
+    p = params(9, 7, 0xFF, 8, 96, 1, 3)
+    o = oracle.sgm(s.left, s.right, 128, 9, 7, 0xFF, 8, 96, 1, 3, uv=False)["disp"]
+    with sgm.Handle(700, 40, 128, p) as h:
+        L, R = cuda(s.left), cuda(s.right)
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK
+        sgm.sgm_debug_stalled_wait(h, L, R)
+        assert sgm.sgm_device_status(h) == sgm.SGM_ERR_TIMEOUT
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK  # the record was cleared
+        for kernel in (sgm.SGM_COST_KERNEL_TENSOR_CORES, sgm.SGM_COST_KERNEL_CUDA_CORES):
+            sgm.sgm_set_cost_kernel(h, kernel)
+            disp = torch.empty((40, 700), dtype=torch.uint8, device="cuda")
+            h.compute(L, R, disp)
+            torch.cuda.synchronize()
+            assert_same(disp.cpu().numpy(), o, f"disparity after the timeout, kernel {kernel}")
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK
+    with sgm.Handle(64, 8, 200, params(5, 5, 0x0F, 4, 24, 1, 3)) as h:
+        img = torch.zeros((8, 64), dtype=torch.uint8, device="cuda")
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_debug_stalled_wait(h, img, img)
+        assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
+
+
 def test_cost_kernel_choice_is_checked():
     with sgm.Handle(64, 8, 200, params(5, 5, 0x0F, 4, 24, 1, 3)) as h:
         with pytest.raises(sgm.SgmError) as e:

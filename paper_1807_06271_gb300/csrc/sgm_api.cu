@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sgm_handle.cuh"
 
 using namespace sgm;
@@ -16,6 +18,12 @@ namespace {
 constexpr int kTimingRing = 1024;
 
 const char *const kStageNames[kNumStages] = {"census", "cost", "aggregate", "wta_lr", "median", "uvmap"};
+// NVTX push/pop range around each stage's launches (host side; a tool attached
+// to the process can select kernels by range, e.g. ncu --nvtx --nvtx-include
+// "sgm:aggregate/").  Stage ranges are not nested in a per-pair range, so they
+// match at the top level of an application that opens none itself.
+const char *const kStageRanges[kNumStages] = {"sgm:census", "sgm:cost", "sgm:aggregate",
+                                              "sgm:wta_lr", "sgm:median", "sgm:uvmap"};
 
 int validate(int W, int H, int D, const sgm_params *p) {
     if (!p || W < 1 || H < 1 || D < 1) return SGM_ERR_INVALID_ARG;
@@ -76,6 +84,7 @@ void harvest(sgm_handle_s *h, TimingRecord &rec) {
 }
 
 TimingRecord *stage_begin(sgm_handle_s *h, int stage, cudaStream_t s) {
+    nvtxRangePushA(kStageRanges[stage]);
     if (!h->timing || !h->recs) return nullptr;
     TimingRecord *rec;
     if (h->rec_count == kTimingRing) {  // ring full: fold the oldest record first
@@ -91,6 +100,7 @@ TimingRecord *stage_begin(sgm_handle_s *h, int stage, cudaStream_t s) {
 }
 
 void stage_end(sgm_handle_s *h, TimingRecord *rec, cudaStream_t s) {
+    nvtxRangePop();
     if (!rec) return;
     cudaEventRecord(rec->stop, s);
     h->rec_count++;

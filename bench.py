@@ -211,6 +211,15 @@ def _oracle_warm(_):
     return os.getpid()
 
 
+def _oracle_pair(task):
+    """One whole pair through the plain oracle (spawned process; no CUDA)."""
+    import oracle
+    left, right, fields = task
+    D, cw, ch, mask, P1, P2, tol, k, uv, cost = fields
+    oracle.sgm(left, right, D, cw, ch, mask, P1, P2, tol, k, uv=uv, cost=cost)
+    return left.shape[0] * left.shape[1] * D
+
+
 class OraclePool:
     """The oracle on every host core at once: one spawned process per core,
     each running whole bands of the pair (the oracle itself stays single
@@ -238,6 +247,13 @@ class OraclePool:
         self.pool.map(_oracle_worker, tasks, chunksize=1)
         dt = time.perf_counter() - t0
         return dt, w.W * rows * w.D * reps * self.procs
+
+    def run_pairs(self, tasks):
+        """Wall time of whole pairs (left, right, fields) spread over the
+        processes, and the DE done."""
+        t0 = time.perf_counter()
+        de = sum(self.pool.map(_oracle_pair, tasks, chunksize=1))
+        return time.perf_counter() - t0, de
 
     def close(self):
         self.pool.close()
@@ -561,10 +577,11 @@ def run_batch(args):
     torch.cuda.set_device(0)
     specs = batch_specs()
     p = sgm.SgmParams(census_w=9, census_h=7, path_mask=0xFF, P1=8, P2=96, lr_tolerance=1, median_k=3)
-    hs, L, R, Dd, U, V = [], [], [], [], [], []
+    hs, L, R, Dd, U, V, pairs = [], [], [], [], [], [], []
     for i, (W, H, D) in enumerate(specs):
         sc = scenes.ground_scene(W, H, D, seed=1807 + 3 + i, n_obstacles=3, dlo=D // 6, dhi=(D * 6) // 7,
                                  texture="value", sigma=2.0, occlusion=0.05)
+        pairs.append((sc.left, sc.right, (D, 9, 7, 0xFF, 8, 96, 1, 3, True, 0)))
         hs.append(sgm.Handle(W, H, D, p))
         L.append(torch.from_numpy(sc.left).cuda())
         R.append(torch.from_numpy(sc.right).cuda())
@@ -606,10 +623,18 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(specs),
                        "de_per_step": de, "tuned_blocks_per_sm": {f"{k[0]}x{k[1]}d{k[2]}": v for k, v in tuned.items()}},
-            "one_pair_per_launch": {"ms_per_step": seq_ms, "value": de / (seq_ms / 1e3) / 1e6}}
-    print(json.dumps(line), flush=True)
+            "one_pair_per_launch": {"ms_per_step": seq_ms, "value": de / (seq_ms / 1e3) / 1e6},
+            "cpu_baseline": None}
     for h in hs:
         h.close()
+    if not args.no_cpu_baseline:
+        # the oracle over the same 64 pairs, whole pairs spread over one process per host core
+        pool = OraclePool()
+        dt, de_cpu = pool.run_pairs(pairs)
+        pool.close()
+        line["cpu_baseline"] = {"value": de_cpu / dt / 1e6, "unit": "MDE/s", "cores": pool.procs, "kind": "oracle",
+                                "sample": f"all {len(pairs)} pairs of the batch once, {dt:.1f} s wall"}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -633,9 +658,31 @@ def run_serve(args):
             "config": {"workload": "serve-8cams-30fps-4GB", "seconds": args.serve_seconds},
             "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "max_ms": sm["max_ms"],
             "frames": sm["frames"], "mde_per_s": sm["mde_per_s"], "slots": sm["slots"],
-            "device_bytes": sm["device_bytes"], "max_queue": sm["max_queue"]}
-    print(json.dumps(line), flush=True)
+            "device_bytes": sm["device_bytes"], "max_queue": sm["max_queue"], "cpu_baseline": None}
     ex.close()
+    if not args.no_cpu_baseline:
+        # the oracle per camera type: one frame each, single thread, and the
+        # frame rate with one frame per host core
+        import oracle
+        per_frame, tasks = {}, []
+        for si, spec in enumerate(specs):
+            left, right = frames[si][0]
+            fields = (spec.D, 9, 7, 0xFF, 8, 96, 1, 3, True, 0)
+            key = f"{spec.W}x{spec.H}d{spec.D}"
+            if key not in per_frame:
+                t0 = time.perf_counter()
+                oracle.sgm(left, right, *fields[:8], uv=True)
+                per_frame[key] = (time.perf_counter() - t0) * 1e3
+            tasks.append((left, right, fields))
+        pool = OraclePool()
+        tasks = (tasks * ((pool.procs + len(tasks) - 1) // len(tasks)))[:max(pool.procs, len(tasks))]
+        dt, _ = pool.run_pairs(tasks)
+        pool.close()
+        line["cpu_baseline"] = {"per_frame_ms": per_frame, "unit": "ms", "cores": 1, "kind": "oracle",
+                                "all_cores_fps": len(tasks) / dt, "all_cores": pool.procs,
+                                "sample": "one frame of each camera type on one core; the camera mix, "
+                                          "one frame per host core, for all_cores_fps"}
+    print(json.dumps(line), flush=True)
     return 0
 
 

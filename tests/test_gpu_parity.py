@@ -119,6 +119,10 @@ CASES = [
     # widths that are not a multiple of a warp's pixel group, 64 disparities
     (301, 9, 60, 5, 5, 0xFF, 4, 24, 1, 3),
     (150, 12, 64, 9, 7, 0x0F, 8, 96, 2, 3),
+    # more rows than 3 WTA CTAs per SM hold on 152 SMs but fewer than 4: the
+    # WTA launcher takes its one-group-ahead variant (other cases take two)
+    (48, 500, 64, 9, 7, 0xFF, 8, 96, 1, 3),
+    (33, 700, 128, 5, 5, 0x0F, 4, 24, 1, 3),
 ]
 
 

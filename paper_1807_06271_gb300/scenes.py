@@ -116,7 +116,10 @@ def add_noise(rng: Rng, img: np.ndarray, sigma: float) -> np.ndarray:
 class Scene:
     left: np.ndarray
     right: np.ndarray
-    gt: np.ndarray  # ground-truth disparity, int16, -1 where the match is occluded
+    # ground-truth disparity of the left image, int16; -1 where ground_scene's
+    # occlusion mask replaced the match.  Pixels hidden in the right view by a
+    # nearer surface keep their own disparity.
+    gt: np.ndarray
     meta: dict = field(default_factory=dict)
 
 

@@ -1,7 +1,9 @@
 """Randomised parity sweep (GPU): seeded draws of shape, disparity range, cost
-kind and window, path set, penalties, LR tolerance, median size and Hamming
-kernel, each compared with the oracle element by element: the cost volume,
-the sum S, the final disparity map and the U-/V-maps."""
+kind and window, path set, penalties, LR tolerance, median size, Hamming
+kernel, row pitch and rectification maps, each compared with the oracle
+element by element: the cost volume, the sum S, the final disparity map and
+the U-/V-maps, through the device entry points and, for some draws, the
+host-buffer one."""
 import numpy as np
 import pytest
 
@@ -61,21 +63,56 @@ def draw_case(seed):
     return W, H, D, sad, cw, ch, mask, P1, P2, tol, k, kernel, left, right
 
 
+def draw_extras(seed, W, H):
+    """Row pitch, rectification maps (or None) and whether to also run the
+    host-buffer entry point; from a stream of its own, so that the draws
+    above stay as they are."""
+    r = np.random.default_rng(19000 + seed)
+    pitch = W + int(r.integers(1, 70)) if r.random() < 0.3 else 0
+    maps = None
+    if r.random() < 0.25:
+        y, x = np.mgrid[0:H, 0:W]
+        # a mostly smooth warp with a few wild entries, some of them outside the image
+        dx = int(r.integers(-3, 4)) + (y // max(1, H // 4)) % 2
+        dy = int(r.integers(-2, 3))
+        maps = []
+        for base, off, n in ((x, 0, W), (y, 0, H), (x, dx, W), (y, dy, H)):
+            m = np.clip(base + off, 0, 0xFFFF).astype(np.uint16)
+            wild = r.random(m.shape) < 0.02
+            m[wild] = r.integers(0, n + 8, int(wild.sum()))
+            maps.append(m)
+    host = r.random() < 0.3
+    return pitch, maps, host
+
+
 @pytest.mark.parametrize("seed", range(100))
 def test_random_configuration_matches_oracle(seed):
     W, H, D, sad, cw, ch, mask, P1, P2, tol, k, kernel, left, right = draw_case(seed)
+    pitch, maps, host = draw_extras(seed, W, H)
     cost = sgm.SGM_COST_SAD if sad else sgm.SGM_COST_CENSUS
     p = sgm.SgmParams(census_w=cw, census_h=ch, path_mask=mask, P1=P1, P2=P2, lr_tolerance=tol,
-                      median_k=k, cost=cost)
-    what = f"W={W} H={H} D={D} {'sad' if sad else 'census'} {cw}x{ch} mask={mask:#x} P={P1}/{P2} tol={tol} k={k} kernel={kernel}"
-    o = oracle.sgm(left, right, D, cw, ch, mask, P1, P2, tol, k, stages=True, cost=cost)
+                      median_k=k, cost=cost, row_pitch=pitch)
+    what = (f"W={W} H={H} D={D} {'sad' if sad else 'census'} {cw}x{ch} mask={mask:#x} P={P1}/{P2} tol={tol} "
+            f"k={k} kernel={kernel} pitch={pitch} rect={maps is not None} host={host}")
+    lo, ro = left, right
+    if maps is not None:
+        lo, ro = oracle.rectify(left, maps[0], maps[1]), oracle.rectify(right, maps[2], maps[3])
+    o = oracle.sgm(lo, ro, D, cw, ch, mask, P1, P2, tol, k, stages=True, cost=cost)
     if sad:
-        C_want = oracle.sad_cost_volume(left, right, D, cw, ch)
+        C_want = oracle.sad_cost_volume(lo, ro, D, cw, ch)
     else:
         C_want = oracle.cost_volume(o["codes_l"], o["codes_r"], D, cw * ch - 1)
     with sgm.Handle(W, H, D, p) as h:
         sgm.sgm_set_cost_kernel(h, kernel)
-        L, R = cuda(left), cuda(right)
+        if maps is not None:
+            dev_maps = [cuda(m.view(np.int16)) for m in maps]
+            sgm.sgm_set_rectification(h, *dev_maps)
+        if pitch:  # rows of `pitch` bytes, the bytes past W filled with a value the path must not read
+            pl, pr = np.full((H, pitch), 77, np.uint8), np.full((H, pitch), 201, np.uint8)
+            pl[:, :W], pr[:, :W] = left, right
+            L, R = cuda(pl), cuda(pr)
+        else:
+            L, R = cuda(left), cuda(right)
         C = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
         sgm.sgm_debug_cost(h, L, R, C, kernel)
         S = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
@@ -91,3 +128,11 @@ def test_random_configuration_matches_oracle(seed):
                                 ("U", u16(U), o["U"]), ("V", u16(V), o["V"])):
             assert got.shape == want.shape, (what, name)
             assert np.array_equal(got, want), f"{what}: {name} differs at {np.argwhere(got != want)[:3].tolist()}"
+        if host:  # packed host rows (the handle's pitch applies to device inputs only)
+            hd = np.empty((H, W), np.uint8)
+            hu = np.empty((D, W), np.uint16)
+            hv = np.empty((H, D), np.uint16)
+            sgm.sgm_compute_host(h, left, right, hd, hu, hv)
+            assert sgm.sgm_device_status(h) == sgm.SGM_OK, what
+            for name, got, want in (("host disp", hd, o["disp"]), ("host U", hu, o["U"]), ("host V", hv, o["V"])):
+                assert np.array_equal(got, want), f"{what}: {name} differs at {np.argwhere(got != want)[:3].tolist()}"

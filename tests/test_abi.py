@@ -100,3 +100,26 @@ def test_binding_has_the_c_names():
         if n in ("sgm_status_string", "sgm_stage_name"):
             continue
         assert hasattr(sgm, n), n
+
+
+def test_product_code_never_reaches_the_oracle():
+    """The package (binding, serving, build, generators) and the CUDA sources
+    neither import, include nor load anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_1807_06271_gb300")
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle|#\s*include\s*[<\"].*oracle)|liboracle|oracle[/\\]", re.M)
+    checked = 0
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn), encoding="utf-8").read()
+                assert not pat.search(text), os.path.join(dirpath, fn)
+                checked += 1
+    assert checked >= 10
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with libsgm.so absent the first call raises."""
+    monkeypatch.setattr(sgm, "_lib", None)
+    monkeypatch.setattr(sgm, "library_path", lambda: str(tmp_path / "libsgm.so"))
+    with pytest.raises(RuntimeError, match="libsgm.so not found"):
+        sgm.load(build_if_missing=False)

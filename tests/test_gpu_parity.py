@@ -527,3 +527,48 @@ def test_sad_handle_has_no_census_codes():
         with pytest.raises(sgm.SgmError) as e:
             sgm.sgm_debug_census(h, img, img, c, c)
         assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# Every blocks-per-SM setting the tuner tries: the aggregation places one
+# long-axis job per (SM, scheduler) slot, so its schedule changes with the
+# number of resident blocks, and its results must not.
+# ---------------------------------------------------------------------------
+
+_TUNE_CASES = {
+    "kitti": lambda: (scenes.scene_for(scenes.KITTI_1242, scenes.workload_seed(1)), scenes.KITTI_1242),
+    "tall": lambda: (scenes.boxes_scene(160, 600, 64, seed=77, n_boxes=5, dlo=2, dhi=60), None),
+}
+_tune_oracle = {}
+
+
+def _tune_case(name):
+    if name not in _tune_oracle:
+        s, w = _TUNE_CASES[name]()
+        if w is None:  # columns are the long axis: 5x5 census, 8 paths
+            cfg = dict(D=64, cw=5, ch=5, mask=0xFF, P1=4, P2=24, tol=1, k=3)
+        else:
+            cfg = dict(D=w.D, cw=w.census_w, ch=w.census_h, mask=w.path_mask, P1=w.P1, P2=w.P2, tol=w.lr_tol,
+                       k=w.median_k)
+        o = oracle.sgm(s.left, s.right, cfg["D"], cfg["cw"], cfg["ch"], cfg["mask"], cfg["P1"], cfg["P2"],
+                       cfg["tol"], cfg["k"], stages=True)
+        _tune_oracle[name] = (s, cfg, o)
+    return _tune_oracle[name]
+
+
+@pytest.mark.parametrize("name", sorted(_TUNE_CASES))
+@pytest.mark.parametrize("bps", [1, 2, 3, 4, 6])
+def test_every_tuner_setting_is_bit_exact(name, bps, monkeypatch):
+    s, c, o = _tune_case(name)
+    H, W = s.left.shape
+    monkeypatch.setenv("SGM_AGG_BLOCKS_PER_SM", str(bps))  # read when the handle is created
+    with sgm.Handle(W, H, c["D"], params(c["cw"], c["ch"], c["mask"], c["P1"], c["P2"], c["tol"], c["k"])) as h:
+        L, R = cuda(s.left), cuda(s.right)
+        S = torch.empty((H, W, c["D"]), dtype=torch.int16, device="cuda")
+        disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        sgm.sgm_debug_sum(h, L, R, S)
+        h.compute(L, R, disp)
+        torch.cuda.synchronize()
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK
+        assert_same(u16(S), o["S"], f"S at {bps} blocks/SM")
+        assert_same(disp.cpu().numpy(), o["disp"], f"disp at {bps} blocks/SM")

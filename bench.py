@@ -260,6 +260,15 @@ class OraclePool:
         self.pool.join()
 
 
+def workload_config(w):
+    """The workload keys of the bench line, the same for both arms."""
+    return {"workload": w.name, "W": w.W, "H": w.H, "D": w.D,
+            "cost": "sad" if w.cost == 1 else "census",
+            "census": f"{w.census_w}x{w.census_h}", "path_mask": w.path_mask,
+            "P1": w.P1, "P2": w.P2, "lr_tol": w.lr_tol, "median_k": w.median_k,
+            "uv_maps": w.uv}
+
+
 def run_reference(args, w, windex):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -286,7 +295,7 @@ def run_reference(args, w, windex):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w.name, "W": w.W, "H": w.H, "D": w.D},
+        "config": dict(workload_config(w), parallelism=f"{pool.procs} host processes"),
         "cpu_baseline": {"value": value, "unit": "MDE/s", "cores": pool.procs, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -530,13 +539,9 @@ def run_ours(args, w, windex):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": w.name, "W": w.W, "H": w.H, "D": w.D,
-                       "cost": "sad" if w.cost == 1 else "census",
-                       "census": f"{w.census_w}x{w.census_h}", "path_mask": w.path_mask,
-                       "P1": w.P1, "P2": w.P2, "lr_tol": w.lr_tol, "median_k": w.median_k,
-                       "uv_maps": w.uv, "parallelism": f"replicas{world}",
-                       "agg_blocks_per_sm": bps if bps is not None else "default",
-                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "config": dict(workload_config(w), parallelism=f"replicas{world}",
+                           agg_blocks_per_sm=bps if bps is not None else "default",
+                           l2="flushed between steps (256 MiB write outside the timed events)"),
             "fps": 1e3 / ms_per_step * world,
             "roofline": roofline,
             "cpu_baseline": cpu,

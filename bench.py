@@ -275,11 +275,11 @@ def run_reference(args, w, windex):
         return 0
     scene = scenes.scene_for(w, rank_seed(windex, 0))
     # Size each step's sample (a band of rows of the pair) so that warm-up plus
-    # the timed steps take about two minutes of host time in total.
+    # the timed steps take about --reference-seconds (two minutes) of host time.
     probe_rows = min(w.H, 16)
     t_probe, _ = time_oracle(w, scene, probe_rows, 1)
     per_row = t_probe / probe_rows
-    budget = 120.0 / max(1, args.steps + args.warmup)
+    budget = args.reference_seconds / max(1, args.steps + args.warmup)
     rows = int(min(w.H, max(8, budget / max(per_row, 1e-9))))
     # every step runs the band once on each host core (one process per core)
     pool = OraclePool()
@@ -708,6 +708,8 @@ def main(argv=None):
                     help="frame: the headline single-pair line; batch: 64 mixed pairs per step; "
                          "serve: 8 Poisson camera streams")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--reference-seconds", type=float, default=120.0,
+                    help="host time the reference arm's warm-up plus timed steps should take")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -62,3 +62,34 @@ def test_oracle_pool_runs_one_band_per_process():
         pool.close()
     assert pool.procs == 2 and dt > 0
     assert de == 2 * w.W * 16 * w.D
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    """`bench.py --impl reference` times the oracle on the host cores and prints
+    one JSON line with the arm's workload keys and a zero-copy e2e."""
+    import json
+    import bench
+    from paper_1807_06271_gb300 import scenes
+    wl = "pair-320x240-d64-census5x5-4path"
+    assert bench.main(["--impl", "reference", "--workload", wl, "--steps", "2", "--warmup", "3",
+                       "--reference-seconds", "3"]) == 0
+    out = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(out) == 1
+    d = json.loads(out[0])
+    assert d["impl"] == "reference" and d["metric"] == "MDE/s" and d["unit"] == "MDE/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (2, 3, 1)
+    assert d["ms_per_step"] > 0 and d["data"] == "synthetic" and d["dtype"] == "u8"
+    want = bench.workload_config(scenes.WORKLOADS[wl])
+    assert {k: d["config"][k] for k in want} == want
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MDE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.main(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]) == 0
+    assert capsys.readouterr().out.strip() == ""

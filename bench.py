@@ -383,11 +383,8 @@ def run_ours(args, w, windex):
     value = whole_job_rate(de * args.steps, world, total_s_max) / 1e6
     ms_per_step = total_s_max / args.steps * 1e3
 
-    # dominant kernel and its roofline
-    dom = max((k for k in stage if stage[k][1] > 0), key=lambda k: stage[k][0])
-    dom_ms = stage[dom][0] / max(stage[dom][1], 1)
+    # the dominant kernel (the aggregation) against the INT32 issue peak
     ops = workload_ops(w)
-    mhz = clocks.get("sm_mhz") or 2070.0
     lanes = 128  # INT32 lanes per SM on GB300 (unified FP32/INT32 datapath)
     peak = int_peak_tops(152, lanes, 2070.0)
     achieved = ops["per_de"] * de / (stage["aggregate"][0] / max(stage["aggregate"][1], 1) / 1e3) / 1e12

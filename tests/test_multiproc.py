@@ -93,3 +93,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.main(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]) == 0
     assert capsys.readouterr().out.strip() == ""
+
+
+def test_roofline_host_arithmetic():
+    """Ops per estimate (7 per path plus the cost), the INT32 issue peak, and
+    traffic taken from a profile summary only when its source digest matches."""
+    import bench
+    from paper_1807_06271_gb300 import scenes
+    ops = bench.workload_ops(scenes.KITTI_1242)          # 8 paths, 62-bit codes
+    assert ops["per_de"] == 7 * 8 + 5 == 61
+    assert bench.workload_ops(scenes.SMALL_320)["per_de"] == 7 * 4 + 2 == 30   # 4 paths, 24-bit codes
+    assert bench.workload_ops(scenes.PAPER_640_SAD)["per_de"] == 7 * 4 + 2 * 5 + 5  # 5x5 SAD
+    assert abs(bench.int_peak_tops() - 152 * 128 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_profiled_traffic_needs_the_current_source(tmp_path, monkeypatch):
+    import bench
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path))
+    (tmp_path / "aggregate_w.md").write_text("# x\n\nsource-digest: 0123abcd\ndram-bytes-per-launch: 636939264\n")
+    assert bench.profiled_traffic("aggregate", "w", "0123abcd") == 636939264.0
+    assert bench.profiled_traffic("aggregate", "w", "ffffffff") is None   # kernel changed since the capture
+    assert bench.profiled_traffic("aggregate", "other", "0123abcd") is None  # no capture for this workload

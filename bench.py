@@ -270,7 +270,7 @@ def workload_config(w):
 
 
 def run_reference(args, w, windex):
-    rank, world, _ = dist_env()
+    rank = dist_env()[0]
     if rank != 0:
         return 0
     scene = scenes.scene_for(w, rank_seed(windex, 0))

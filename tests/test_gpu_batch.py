@@ -134,7 +134,7 @@ def test_64_pair_mixed_batch_equals_single_pair_launches():
         assert np.array_equal(u16(b.U[i]), u) and np.array_equal(u16(b.V[i]), v), i
     small = [i for i, sp in enumerate(specs) if sp[:2] == (320, 240)][:2]
     for i in small:
-        W, H, D = specs[i]
+        D = specs[i][2]
         s = b.scenes[i]
         o = oracle.sgm(s.left, s.right, D, 9, 7, sgm.SGM_PATHS_8, 8, 96, 1, 3)
         assert np.array_equal(b.Dd[i].cpu().numpy(), o["disp"]), i

@@ -71,10 +71,41 @@ def _create(W, H, D, **kw):
     (10, 10, 16, dict(cost=1, census_w=11, census_h=13, P1=0, P2=0, path_mask=1), sgm.SGM_ERR_UNSUPPORTED),
     (10, 10, 16, dict(cost=1, census_w=17, census_h=1, P1=0, P2=0, path_mask=1), sgm.SGM_ERR_UNSUPPORTED),
     (10, 10, 16, dict(cost=1, census_w=4, census_h=5), sgm.SGM_ERR_INVALID_ARG),  # even window
+    (10, 10, 16, dict(census_w=5, census_h=4), sgm.SGM_ERR_INVALID_ARG),
+    (10, 10, 16, dict(census_w=-1), sgm.SGM_ERR_INVALID_ARG),
+    (1, 65536, 1, dict(path_mask=1), sgm.SGM_ERR_UNSUPPORTED),     # rows index with 16 bits
+    (8193, 1, 1, dict(path_mask=1), sgm.SGM_ERR_UNSUPPORTED),
+    (10, 10, 16, dict(census_w=9, census_h=7, P1=0, P2=194), sgm.SGM_ERR_UNSUPPORTED),  # 62 + 194 = 256
+    (10, 10, 16, dict(cost=1, census_w=5, census_h=5, P1=0, P2=26392, path_mask=1), sgm.SGM_ERR_UNSUPPORTED),
+    # 32-bit lane-chunk indices of the planes: 8192 x 65535 x 8 paths x 32 lanes
+    (8192, 65535, 255, dict(path_mask=0xFF), sgm.SGM_ERR_UNSUPPORTED),
 ])
 def test_create_rejects_bad_arguments_on_host(W, H, D, kw, want):
     rc, h = _create(W, H, D, **kw)
     assert rc == want and h is None
+
+
+@pytest.mark.parametrize("W,H,D,kw", [
+    (1, 65535, 1, dict(path_mask=1)),                                 # largest height
+    (8192, 1, 1, dict(path_mask=1)),                                  # largest width
+    (4, 4, 255, {}),                                                  # largest D
+    (10, 10, 16, dict(census_w=9, census_h=7, P1=0, P2=193)),         # 62 + 193 = 255
+    (10, 10, 16, dict(median_k=7)),
+    (10, 10, 16, dict(median_k=0)),
+    (10, 10, 16, dict(median_k=1)),
+    (10, 10, 16, dict(row_pitch=10)),
+    (10, 10, 16, dict(cost=1, census_w=5, census_h=5, P1=0, P2=26391, path_mask=1)),  # 6375 + 26391 = 0x7FFE
+    (10, 10, 16, dict(cost=1, census_w=15, census_h=1, P1=0, P2=0, path_mask=1)),     # widest SAD window
+    (10, 10, 16, dict(census_w=1, census_h=1, P1=0, P2=0)),                           # 0-bit census
+])
+def test_create_accepts_the_limits(W, H, D, kw):
+    """Values on the accepted side of each limit pass the host checks: without
+    a GPU the call then fails at the device query (SGM_ERR_CUDA), with one it
+    creates a (small) handle."""
+    rc, h = _create(W, H, D, **kw)
+    assert rc in (sgm.SGM_OK, sgm.SGM_ERR_CUDA), rc
+    if h:
+        assert sgm.load().sgm_destroy(h) == sgm.SGM_OK
 
 
 def test_null_arguments_are_rejected():

@@ -154,3 +154,36 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(sgm, "library_path", lambda: str(tmp_path / "libsgm.so"))
     with pytest.raises(RuntimeError, match="libsgm.so not found"):
         sgm.load(build_if_missing=False)
+
+
+def _handle_functions():
+    """Declared functions whose first parameter is an sgm_handle."""
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fn)).read(), flags=re.S)
+            names += re.findall(r"^\s*int\s+(\w+)\s*\(\s*sgm_handle\s+\w+\s*[,)]", text, re.M)
+    return sorted(set(names))
+
+
+def test_every_handle_entry_point_rejects_a_null_handle():
+    """Null handle, zero or null everything else: SGM_ERR_INVALID_ARG before
+    any device call (so this runs without a GPU)."""
+    lib = sgm.load()
+    names = _handle_functions()
+    assert len(names) >= 20
+    for n in names:
+        fn = getattr(lib, n)
+        numeric = (ctypes.c_int, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_longlong, ctypes.c_float, ctypes.c_size_t)
+        args = [0 if t in numeric else None for t in fn.argtypes]
+        assert fn(*args) == sgm.SGM_ERR_INVALID_ARG, n
+
+
+def test_static_entry_point_checks_before_any_device_call():
+    lib = sgm.load()
+    bad = sgm.SgmParams(census_w=4)._c()
+    assert lib.sgm_compute_static(10, 10, 16, ctypes.byref(bad), None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    good = sgm.SgmParams()._c()
+    assert lib.sgm_compute_static(10, 10, 16, ctypes.byref(good), None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_compute_static(10, 10, 16, None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_debug_fail_alloc(-1) == sgm.SGM_ERR_INVALID_ARG

@@ -3,7 +3,8 @@
 definitions in plain Python loops, sharing nothing with the oracle's C code:
 
 - census (Sec. 3.1.2, reading R1) by comparing every window neighbour;
-- the Hamming cost of Eq. 1 (R2 outside the image) by counting bits;
+- the Hamming cost of Eq. 1 (R2 outside the image) by counting bits, or the
+  SAD cost (R13) as a clamped window sum of absolute differences;
 - each path of Eq. 2 (R3) as the exhaustive minimum over all disparity
   sequences along the path, minus the predecessor's minimum;
 - S, both winners-take-all (R4, R5), the LR check (R6), the median (R7) and
@@ -45,6 +46,26 @@ def bf_cost(cl, cr, D, nbits):
     return C
 
 
+def bf_sad(left, right, D, ww, wh):
+    H, W = left.shape
+    C = np.zeros((H, W, D), np.int64)
+    for y in range(H):
+        for x in range(W):
+            for d in range(D):
+                if x - d < 0:
+                    C[y, x, d] = ww * wh * 255
+                    continue
+                tot = 0
+                for v in range(-(wh // 2), wh // 2 + 1):
+                    for u in range(-(ww // 2), ww // 2 + 1):
+                        yy = min(max(y + v, 0), H - 1)
+                        xl = min(max(x + u, 0), W - 1)
+                        xr = min(max(x - d + u, 0), W - 1)
+                        tot += abs(int(left[yy, xl]) - int(right[yy, xr]))
+                C[y, x, d] = tot
+    return C
+
+
 def bf_path(C, dx, dy, P1, P2):
     """L_r(p, d) = min over disparity sequences along the path ending at p with
     d of (sum of costs + 0 / P1 / P2 per step), minus the same minimum over all
@@ -72,11 +93,14 @@ def bf_path(C, dx, dy, P1, P2):
     return L
 
 
-def bf_pipeline(left, right, D, cw, ch, mask, P1, P2, tol, k):
+def bf_pipeline(left, right, D, cw, ch, mask, P1, P2, tol, k, sad=False):
     H, W = left.shape
-    nbits = cw * ch - 1
-    cl, cr = bf_census(left, cw, ch), bf_census(right, cw, ch)
-    C = bf_cost(cl, cr, D, nbits)
+    if sad:
+        cl = cr = None
+        C = bf_sad(left, right, D, cw, ch)
+    else:
+        cl, cr = bf_census(left, cw, ch), bf_census(right, cw, ch)
+        C = bf_cost(cl, cr, D, cw * ch - 1)
     S = np.zeros((H, W, D), np.int64)
     for r, (dx, dy) in enumerate(oracle.DIRECTIONS):
         if (mask >> r) & 1:
@@ -145,3 +169,26 @@ def test_oracle_equals_brute_force_composition(case):
     assert np.array_equal(got["disp"].astype(np.int64), want["disp"])
     assert np.array_equal(got["U"].astype(np.int64), want["U"])
     assert np.array_equal(got["V"].astype(np.int64), want["V"])
+
+
+SAD_CASES = [
+    # W, H, D, window, path mask, P1, P2, LR tolerance, median size, seed
+    (6, 4, 3, 3, 3, 0x0F, 200, 800, 1, 3, 11),   # the paper's SAD penalties
+    (5, 5, 3, 5, 5, 0x55, 50, 400, 0, 3, 12),
+    (7, 3, 2, 3, 1, 0xFF, 0, 0, -1, 1, 13),
+]
+
+
+@pytest.mark.parametrize("case", SAD_CASES, ids=lambda c: "x".join(map(str, c[:3])) + f"-m{c[5]:02x}")
+def test_sad_oracle_equals_brute_force_composition(case):
+    W, H, D, ww, wh, mask, P1, P2, tol, k, seed = case
+    r = np.random.default_rng(4300 + seed)
+    left = r.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.roll(left, 1, axis=1)
+    right[:, 0] = r.integers(0, 256, H)
+    want = bf_pipeline(left, right, D, ww, wh, mask, P1, P2, tol, k, sad=True)
+    got = oracle.sgm(left, right, D, ww, wh, mask, P1, P2, tol, k, stages=True, cost=oracle.COST_SAD)
+    assert np.array_equal(oracle.sad_cost_volume(left, right, D, ww, wh).astype(np.int64), want["C"])
+    for key, gkey in (("S", "S"), ("D_left", "DL"), ("D_right", "DR"), ("lr", "lr"), ("disp", "disp"),
+                      ("U", "U"), ("V", "V")):
+        assert np.array_equal(got[gkey].astype(np.int64), want[key]), key

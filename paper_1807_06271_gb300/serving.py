@@ -45,7 +45,8 @@ class StreamSpec:
 
 def slot_device_bytes(spec: StreamSpec) -> int:
     """Device memory of one slot: census codes, cost volume, path planes,
-    LR map, a work counter, and the slot's input/output buffers."""
+    LR map, the aggregation's work-queue state (4224 bytes) with the device
+    status word, and the slot's input/output buffers."""
     npx = spec.W * spec.H
     lanes = 1
     while lanes * 8 < spec.D:
@@ -53,7 +54,7 @@ def slot_device_bytes(spec: StreamSpec) -> int:
     Dp = 8 * lanes
     code_bytes = 4 if spec.census_w * spec.census_h - 1 <= 32 else 8
     npaths = bin(spec.path_mask).count("1")
-    scratch = 2 * npx * code_bytes + npx * Dp + npaths * npx * Dp + npx + 4
+    scratch = 2 * npx * code_bytes + npx * Dp + npaths * npx * Dp + npx + 4224 + 4
     io = 2 * npx + npx + 2 * spec.D * spec.W + 2 * spec.H * spec.D
     return scratch + 2 * io
 

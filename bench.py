@@ -70,25 +70,73 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     return units_per_rank * world / seconds_max
 
 
-def workload_ops(w) -> dict:
-    """Algorithmic integer operations per disparity estimate for the
-    aggregation kernel: per enabled path 3 min + 2 add + 1 sub + 1 running
-    min = 7; the matching cost once per estimate: for the census cost XOR +
-    POPC for codes of up to 32 bits (2), two of each plus an add for 64-bit
-    codes (5); for the SAD cost, separable, an absolute difference and an add
-    per window row plus an add per window column (2 wh + ww)."""
+def aggregation_ops(w) -> dict:
+    """Algorithmic integer operations per disparity estimate of the
+    aggregation kernel alone: per enabled path 3 min + 2 add + 1 sub + 1
+    running min = 7 (Eq. 2).  The matching cost runs in its own kernel."""
     npaths = bin(w.path_mask).count("1")
-    nbits = w.census_w * w.census_h - 1
+    return {"per_path": 7, "paths": npaths, "per_de": 7 * npaths}
+
+
+def cost_ops(w) -> int:
+    """Operations per estimate of the matching cost (Eq. 1): XOR + POPC for
+    codes of up to 32 bits (2), two of each plus an add for 64-bit codes (5);
+    the SAD cost, separable, an absolute difference and an add per window row
+    plus an add per window column (2 wh + ww)."""
     if w.cost == 1:
-        cost = 2 * w.census_h + w.census_w
-    else:
-        cost = 2 if nbits <= 32 else 5
-    return {"per_path": 7, "paths": npaths, "cost": cost, "per_de": 7 * npaths + cost}
+        return 2 * w.census_h + w.census_w
+    return 2 if w.census_w * w.census_h - 1 <= 32 else 5
 
 
-def int_peak_tops(sm_count=152, int_lanes_per_sm=128, mhz=2070.0) -> float:
-    """32-bit integer add/min/logic issue peak: SMs x INT32 lanes x clock."""
-    return sm_count * int_lanes_per_sm * mhz * 1e6 / 1e12
+def popc_per_de(w) -> int:
+    return 0 if w.cost == 1 else (1 if w.census_w * w.census_h - 1 <= 32 else 2)
+
+
+def path_ops(w) -> int:
+    """Whole-path integer operations per estimate: the aggregation (7 per
+    path), the cost once, R - 1 adds summing the paths and about 4 for the two
+    winner-takes-all searches (72 for the 8-path 9x7 workload, 37 for the
+    4-path 5x5 ones)."""
+    npaths = bin(w.path_mask).count("1")
+    return 7 * npaths + cost_ops(w) + (npaths - 1) + 4
+
+
+def path_hbm_bytes_per_de(w) -> float:
+    """Bytes per estimate that the path must move through HBM at the least.
+    When the enabled directions run both ways along a scanline, one sweep's
+    16-bit partial sum has to be written and read back once (4 B); when all of
+    them are causal in one top-down sweep, only the images in and the map out
+    (3 bytes per pixel)."""
+    fwd = w.path_mask & 0x55
+    bwd = w.path_mask & 0xAA
+    return 4.0 if (fwd and bwd) else 3.0 / w.D
+
+
+def measured_hbm_gbs():
+    """(GB/s, basis): the measured copy bandwidth of the GB300s,
+    else the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        if v > 0:
+            return v, "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return 6800.0, "fallback"
+
+
+def int_peaks(sgm) -> dict:
+    """Measured integer issue rates (best of three launches of the library's
+    probe kernel): the add/min mix in lane operations per second, the packed
+    16-bit min/add mix counted per 16-bit operation (two per instruction), and
+    POPC (one of the two operations of the xor/popc mix)."""
+    best = {}
+    for name, kind in (("int32", sgm.SGM_PROBE_INT32_ADD_MIN), ("u16x2", sgm.SGM_PROBE_U16X2_MIN_ADD),
+                       ("popc_xor", sgm.SGM_PROBE_POPC_XOR)):
+        best[name] = max(sgm.sgm_probe_int_rate(kind)[0] for _ in range(3))
+    return {"int32_tops": best["int32"] / 1e12, "u16x2_tops": 2 * best["u16x2"] / 1e12,
+            "popc_tops": best["popc_xor"] / 2 / 1e12,
+            "basis": "sgm_probe_int_rate: 8 blocks x 256 threads per SM, 8 independent chains per thread"}
 
 
 def kernel_source_digest(files) -> str:
@@ -308,6 +356,171 @@ def run_reference(args, w, windex):
 # the CUDA arm
 # ---------------------------------------------------------------------------
 
+def sgm_params_of(sgm, w):
+    return sgm.SgmParams(census_w=w.census_w, census_h=w.census_h, path_mask=w.path_mask,
+                         P1=w.P1, P2=w.P2, lr_tolerance=w.lr_tol, median_k=w.median_k, cost=w.cost)
+
+
+class FramePair:
+    """One workload's pair resident on the device, its handle and outputs."""
+
+    def __init__(self, sgm, torch, w, seed, autotune):
+        self.w = w
+        self.scene = scenes.scene_for(w, seed)
+        self.params = sgm_params_of(sgm, w)
+        self.h = sgm.Handle(w.W, w.H, w.D, self.params)
+        self.left = torch.from_numpy(self.scene.left).cuda()
+        self.right = torch.from_numpy(self.scene.right).cuda()
+        self.disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
+        self.umap = torch.empty((w.D, w.W), dtype=torch.int16, device="cuda")
+        self.vmap = torch.empty((w.H, w.D), dtype=torch.int16, device="cuda")
+        # the aggregation kernel's resident blocks per SM, chosen by the
+        # library's own tuner for this shape (a user calls the same entry point)
+        self.bps = (sgm.sgm_autotune(self.h, self.left, self.right, self.disp,
+                                     torch.cuda.current_stream()) if autotune else None)
+
+    def step(self, stream):
+        self.h.compute(self.left, self.right, self.disp, stream)
+        if self.w.uv:
+            self.h.uvmap(self.disp, self.umap, self.vmap, stream)
+
+    def close(self):
+        self.h.close()
+
+
+def timed_steps(torch, fp, stream, flush, steps):
+    """CUDA-event time of each of `steps` steps, L2 flushed before each
+    (outside the events)."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        fp.step(stream)
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, stops)]
+
+
+def stage_pass(sgm, fp, stream, flush, n):
+    """Per-stage kernel times from a separate pass with stage events recorded
+    around every kernel (the timed steps run without them)."""
+    sgm.sgm_set_timing(fp.h, True)
+    sgm.sgm_get_stage_times(fp.h)  # reset
+    for i in range(n):
+        flush.fill_(i & 0xFF)
+        fp.step(stream)
+    stage = sgm.sgm_get_stage_times(fp.h)
+    sgm.sgm_set_timing(fp.h, False)
+    return stage
+
+
+def e2e_run(torch, sgm, fp, stream, steps, world=1):
+    """End to end through the pipelined host-buffer entry point, as a camera
+    loop uses it: two pinned host buffer sets in turn, a set reused once the
+    frame that last used it has been collected.  Every step uploads its pair
+    and downloads its disparity map (and U/V maps); frames run back to back."""
+    w, h = fp.w, fp.h
+    sets = []
+    for _ in range(2):
+        sets.append((torch.from_numpy(fp.scene.left).pin_memory(), torch.from_numpy(fp.scene.right).pin_memory(),
+                     torch.empty((w.H, w.W), dtype=torch.uint8).pin_memory(),
+                     torch.empty((w.D, w.W), dtype=torch.int16).pin_memory() if w.uv else None,
+                     torch.empty((w.H, w.D), dtype=torch.int16).pin_memory() if w.uv else None))
+    for i in range(2):
+        sgm.sgm_host_wait(h, sgm.sgm_compute_host_async(h, *sets[i], stream))
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(steps):
+        if i >= 2:
+            sgm.sgm_host_wait(h, tickets[i - 2])
+        tickets.append(sgm.sgm_compute_host_async(h, *sets[i & 1], stream))
+    sgm.sgm_host_wait(h, tickets[-2])
+    sgm.sgm_host_wait(h, tickets[-1])
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    return {"value": whole_job_rate(w.de_per_frame * steps, world, e2e_s) / 1e6, "unit": "MDE/s",
+            "h2d_bytes_per_step": 2 * w.W * w.H,
+            "d2h_bytes_per_step": w.W * w.H + (2 * w.D * w.W + 2 * w.H * w.D if w.uv else 0),
+            "steps": steps, "api": "sgm_compute_host_async + sgm_host_wait"}
+
+
+def kernel_rooflines(w, stage, peaks, hbm_gbs):
+    """Each kernel of the path against the resource that bounds it, from the
+    stage pass's mean event times."""
+    de = w.de_per_frame
+    npaths = bin(w.path_mask).count("1")
+    lanes = 1
+    while 8 * lanes < w.D:
+        lanes *= 2
+    Dp, eb = 8 * lanes, (2 if w.cost == 1 else 1)
+    out = {}
+
+    def mean_s(k):
+        t, n = stage.get(k, (0.0, 0))
+        return t / n / 1e3 if n else None
+
+    t = mean_s("aggregate")
+    if t:
+        ops = aggregation_ops(w)["per_de"]
+        a = ops * de / t / 1e12
+        out["aggregate"] = {"bound": "alu", "ops_per_de": ops, "achieved_tops": a, "frac": a / peaks["int32_tops"],
+                            "frac_packed": a / peaks["u16x2_tops"], "us": t * 1e6}
+    t = mean_s("cost")
+    if t:
+        if w.cost == 1:
+            ops = cost_ops(w)
+            a = ops * de / t / 1e12
+            out["cost"] = {"bound": "alu", "ops_per_de": ops, "achieved_tops": a, "frac": a / peaks["int32_tops"],
+                           "us": t * 1e6}
+        else:
+            pc = popc_per_de(w)
+            a = pc * de / t / 1e12
+            out["cost"] = {"bound": "popc", "popc_per_de": pc, "achieved_tpopc": a, "frac": a / peaks["popc_tops"],
+                           "us": t * 1e6}
+    t = mean_s("wta_lr")
+    if t:
+        byts = w.W * w.H * (npaths * Dp * eb + 1)
+        a = byts / t / 1e9
+        out["wta_lr"] = {"bound": "hbm", "bytes": byts, "achieved_gbs": a, "frac": a / hbm_gbs, "us": t * 1e6}
+    return out
+
+
+def path_roofline(w, value_mde, peaks, hbm_gbs):
+    """The whole per-frame path: min(integer bound, HBM bound) in MDE/s and
+    the fraction the measured throughput reaches."""
+    ops = path_ops(w)
+    byts = path_hbm_bytes_per_de(w)
+    int_bound = peaks["int32_tops"] * 1e12 / ops / 1e6
+    hbm_bound = hbm_gbs * 1e9 / byts / 1e6
+    roof = min(int_bound, hbm_bound)
+    return {"ops_per_de": ops, "hbm_bytes_per_de": byts, "int_bound_mde_s": int_bound,
+            "hbm_bound_mde_s": hbm_bound, "bound": "alu" if int_bound <= hbm_bound else "hbm",
+            "roofline_mde_s": roof, "achieved_mde_s": value_mde, "frac": value_mde / roof}
+
+
+def per_config_line(torch, sgm, w, windex, steps, stream, flush, peaks, hbm_gbs):
+    """One workload timed as the headline is (L2 flushed between steps, CUDA
+    events on the stream), plus a short end-to-end run and its stage times."""
+    fp = FramePair(sgm, torch, w, rank_seed(windex, 0), autotune=True)
+    for _ in range(3):
+        fp.step(stream)
+    torch.cuda.synchronize()
+    ms = timed_steps(torch, fp, stream, flush, steps)
+    ms_per_step = sum(ms) / len(ms)
+    value = w.de_per_frame / (ms_per_step / 1e3) / 1e6
+    stage = stage_pass(sgm, fp, stream, flush, min(steps, 50))
+    e2e = e2e_run(torch, sgm, fp, stream, max(3, min(steps, 50)))
+    line = {"config": workload_config(w), "value": value, "unit": "MDE/s", "ms_per_step": ms_per_step,
+            "fps": 1e3 / ms_per_step, "steps": steps, "e2e": e2e, "agg_blocks_per_sm": fp.bps,
+            "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stage.items() if v[1]},
+            "kernels": kernel_rooflines(w, stage, peaks, hbm_gbs),
+            "path_roofline": path_roofline(w, value, peaks, hbm_gbs)}
+    fp.close()
+    return line
+
+
 def run_ours(args, w, windex):
     import numpy as np
     import torch
@@ -320,81 +533,52 @@ def run_ours(args, w, windex):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    scene = scenes.scene_for(w, rank_seed(windex, rank))
-    params = sgm.SgmParams(census_w=w.census_w, census_h=w.census_h, path_mask=w.path_mask,
-                           P1=w.P1, P2=w.P2, lr_tolerance=w.lr_tol, median_k=w.median_k,
-                           cost=w.cost)
-    h = sgm.Handle(w.W, w.H, w.D, params)
     stream = torch.cuda.current_stream()
-    left = torch.from_numpy(scene.left).cuda()
-    right = torch.from_numpy(scene.right).cuda()
-    disp = torch.empty((w.H, w.W), dtype=torch.uint8, device="cuda")
-    umap = torch.empty((w.D, w.W), dtype=torch.int16, device="cuda")
-    vmap = torch.empty((w.H, w.D), dtype=torch.int16, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
-    def step():
-        h.compute(left, right, disp, stream)
-        if w.uv:
-            h.uvmap(disp, umap, vmap, stream)
-
-    # the aggregation kernel's resident blocks per SM, chosen by the library's
-    # own tuner for this shape (a user calls the same entry point)
-    bps = sgm.sgm_autotune(h, left, right, disp, stream) if not args.no_autotune else None
+    peaks = int_peaks(sgm)
+    hbm_gbs, hbm_of = measured_hbm_gbs()
+    fp = FramePair(sgm, torch, w, rank_seed(windex, rank), autotune=not args.no_autotune)
+    h, left, right, disp, umap, vmap = fp.h, fp.left, fp.right, fp.disp, fp.umap, fp.vmap
+    params, scene, bps = fp.params, fp.scene, fp.bps
     for _ in range(args.warmup):
-        step()
+        fp.step(stream)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.2)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.mark()
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)  # evict L2 between steps (outside the timed events)
-        starts[i].record(stream)
-        step()
-        stops[i].record(stream)
-    torch.cuda.synchronize()
+    step_ms = timed_steps(torch, fp, stream, flush, args.steps)
     wall = time.perf_counter() - wall0
     sampler.mark()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    # Per-stage kernel times come from a separate pass with stage events
-    # recorded around every kernel (outside the timed steps above, whose
-    # kernels run back to back without them).
-    sgm.sgm_set_timing(h, True)
-    sgm.sgm_get_stage_times(h)  # reset
-    for i in range(min(args.steps, 200)):
-        flush.fill_(i & 0xFF)
-        step()
-    stage = sgm.sgm_get_stage_times(h)
-    sgm.sgm_set_timing(h, False)
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    stage = stage_pass(sgm, fp, stream, flush, min(args.steps, 200))
     total_s = sum(step_ms) / 1e3
     total_s_max = reduce_max(total_s, world)
     de = w.de_per_frame
     value = whole_job_rate(de * args.steps, world, total_s_max) / 1e6
     ms_per_step = total_s_max / args.steps * 1e3
 
-    # the dominant kernel (the aggregation) against the INT32 issue peak
-    ops = workload_ops(w)
-    lanes = 128  # INT32 lanes per SM on GB300 (unified FP32/INT32 datapath)
-    peak = int_peak_tops(152, lanes, 2070.0)
-    achieved = ops["per_de"] * de / (stage["aggregate"][0] / max(stage["aggregate"][1], 1) / 1e3) / 1e12
+    # the dominant kernel (the aggregation) against the measured INT32 issue
+    # rate, and the whole path against min(integer bound, HBM bound)
+    kernels = kernel_rooflines(w, stage, peaks, hbm_gbs)
+    agg = kernels["aggregate"]
     digest = kernel_source_digest(["paper_1807_06271_gb300/csrc/aggregate.cu",
                                    "paper_1807_06271_gb300/csrc/sgm_internal.cuh"])
     traffic = profiled_traffic("aggregate", w.name, digest)
-    roofline = {"bound": "alu", "kernel": "aggregate", "achieved": achieved, "peak": peak,
-                "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
-                "ops_per_de": ops["per_de"], "peak_basis": f"152 SMs x {lanes} INT32 lanes x 2070 MHz",
-                "of": "derived"}
+    path = path_roofline(w, value / world, peaks, hbm_gbs)
+    roofline = {"bound": "alu", "kernel": "aggregate", "achieved": agg["achieved_tops"],
+                "peak": peaks["int32_tops"], "unit": "Tops/s", "frac": agg["frac"], "traffic": traffic,
+                "ops_per_de": agg["ops_per_de"], "of": "measured", "peak_basis": peaks["basis"],
+                "peak_packed": peaks["u16x2_tops"], "frac_packed": agg["frac_packed"],
+                "path_frac": path["frac"], "path": path, "kernels": kernels,
+                "hbm_peak_gbs": hbm_gbs, "hbm_peak_of": hbm_of}
 
     # Consecutive pairs on two handles and two streams, so that one pair's
     # HBM-bound WTA overlaps the next pair's aggregation (how a stream of
@@ -437,35 +621,7 @@ def run_ours(args, w, windex):
                        "value": de / (ms2 / 1e3) / 1e6, "unit": "MDE/s"}
         h2.close()
 
-    # End to end through the pipelined host-buffer entry point, as a camera
-    # loop uses it: two pinned host buffer sets in turn, a set reused once the
-    # frame that last used it has been collected.  Every step uploads its pair
-    # and downloads its disparity map (and U/V maps); frames run back to back
-    # (the per-step working set, cost volume and planes, exceeds L2).
-    e2e_steps = max(3, min(args.steps, 200))
-    sets = []
-    for _ in range(2):
-        sets.append((torch.from_numpy(scene.left).pin_memory(), torch.from_numpy(scene.right).pin_memory(),
-                     torch.empty((w.H, w.W), dtype=torch.uint8).pin_memory(),
-                     torch.empty((w.D, w.W), dtype=torch.int16).pin_memory() if w.uv else None,
-                     torch.empty((w.H, w.D), dtype=torch.int16).pin_memory() if w.uv else None))
-    for i in range(2):
-        sgm.sgm_host_wait(h, sgm.sgm_compute_host_async(h, *sets[i], stream))
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    tickets = []
-    for i in range(e2e_steps):
-        if i >= 2:
-            sgm.sgm_host_wait(h, tickets[i - 2])
-        tickets.append(sgm.sgm_compute_host_async(h, *sets[i & 1], stream))
-    sgm.sgm_host_wait(h, tickets[-2])
-    sgm.sgm_host_wait(h, tickets[-1])
-    e2e_s = reduce_max(time.perf_counter() - t0, world)
-    e2e = {"value": whole_job_rate(de * e2e_steps, world, e2e_s) / 1e6, "unit": "MDE/s",
-           "h2d_bytes_per_step": 2 * w.W * w.H,
-           "d2h_bytes_per_step": w.W * w.H + (2 * w.D * w.W + 2 * w.H * w.D if w.uv else 0),
-           "steps": e2e_steps, "api": "sgm_compute_host_async + sgm_host_wait"}
+    e2e = e2e_run(torch, sgm, fp, stream, max(3, min(args.steps, 200)), world)
 
     # next rows, timed after the headline loop: map post-processing (Sec. 3.2)
     # and the pipeline reading its inputs through identity rectification maps
@@ -496,23 +652,6 @@ def run_ours(args, w, windex):
     sgm.sgm_set_timing(h, False)
     sgm.sgm_set_rectification(h)
     extras["census_rectified_us"] = rect_stage["census"][0] / max(rect_stage["census"][1], 1) * 1e3
-    # the Hamming cost (Eq. 1) on each of its two kernels, same stage timing
-    if w.cost == 0 and 16 < w.D <= 128:
-        kernels = {}
-        for name, kern in (("cuda_cores", sgm.SGM_COST_KERNEL_CUDA_CORES),
-                           ("tensor_cores", sgm.SGM_COST_KERNEL_TENSOR_CORES)):
-            sgm.sgm_set_cost_kernel(h, kern)
-            for _ in range(3):
-                h.compute(left, right, disp, stream)
-            sgm.sgm_set_timing(h, True)
-            sgm.sgm_get_stage_times(h)
-            for _ in range(50):
-                h.compute(left, right, disp, stream)
-            st = sgm.sgm_get_stage_times(h)
-            sgm.sgm_set_timing(h, False)
-            kernels[name] = st["cost"][0] / max(st["cost"][1], 1) * 1e3
-        sgm.sgm_set_cost_kernel(h, sgm.SGM_COST_KERNEL_AUTO)
-        extras["cost_kernel_us"] = kernels
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -527,6 +666,19 @@ def run_ours(args, w, windex):
                           f"core, {dt:.1f} s wall; single thread: {de1 / dt1 / 1e6:.2f} MDE/s "
                           f"({reps} pair(s), {dt1:.1f} s)"),
                "single_thread_value": de1 / dt1 / 1e6}
+
+    # every other workload of the metric, timed the same way (rank 0, one GPU)
+    per_config = None
+    if rank == 0 and world == 1 and not args.no_per_config:
+        per_config = {}
+        for name, wi in sorted(WORKLOAD_INDEX.items(), key=lambda kv: kv[1]):
+            if name == w.name:
+                continue
+            per_config[name] = per_config_line(torch, sgm, scenes.WORKLOADS[name], wi, min(args.steps, 50),
+                                               stream, flush, peaks, hbm_gbs)
+        per_config["batch-64-mixed-census9x7-8path"] = batch_summary(torch, sgm, steps=min(args.steps, 10),
+                                                                     warmup=3)
+        per_config["serve-8cams-30fps-4GB"] = serve_summary(torch, args.line_serve_seconds)
 
     # census, cost, aggregate, wta_lr, median (a device copy when off), U/V
     launches_per_step = 4 + (1 if w.median_k > 1 else 0) + (1 if w.uv else 0)
@@ -548,10 +700,11 @@ def run_ours(args, w, windex):
             "concurrency": concurrency,
             "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stage.items() if v[1]},
             "next_rows": extras,
+            "per_config": per_config,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
-    h.close()
+    fp.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -569,6 +722,79 @@ def batch_specs(n=64, seed=1807 + 3):
     return [(sizes[a][0], sizes[a][1], (64, 128)[b]) for a, b in zip(si, di)]
 
 
+class BatchSet:
+    """The 64 mixed pairs of the batched workload (9x7 census, 8 paths, P1=8,
+    P2=96, LR 1, 3x3 median, U/V maps; sizes from {320x240, 640x480,
+    1242x375, 1280x720}, D from {64, 128}, per-pair seeds), their handles
+    (tuned per shape by sgm_autotune) and device buffers."""
+
+    def __init__(self, torch, sgm):
+        self.specs = batch_specs()
+        p = sgm.SgmParams(census_w=9, census_h=7, path_mask=0xFF, P1=8, P2=96, lr_tolerance=1, median_k=3)
+        self.hs, self.L, self.R, self.Dd, self.U, self.V, self.pairs = [], [], [], [], [], [], []
+        for i, (W, H, D) in enumerate(self.specs):
+            sc = scenes.ground_scene(W, H, D, seed=1807 + 3 + i, n_obstacles=3, dlo=D // 6, dhi=(D * 6) // 7,
+                                     texture="value", sigma=2.0, occlusion=0.05)
+            self.pairs.append((sc.left, sc.right, (D, 9, 7, 0xFF, 8, 96, 1, 3, True, 0)))
+            self.hs.append(sgm.Handle(W, H, D, p))
+            self.L.append(torch.from_numpy(sc.left).cuda())
+            self.R.append(torch.from_numpy(sc.right).cuda())
+            self.Dd.append(torch.empty((H, W), dtype=torch.uint8, device="cuda"))
+            self.U.append(torch.empty((D, W), dtype=torch.int16, device="cuda"))
+            self.V.append(torch.empty((H, D), dtype=torch.int16, device="cuda"))
+        self.tuned = {}
+        for i, (W, H, D) in enumerate(self.specs):
+            if (W, H, D) not in self.tuned:
+                self.tuned[(W, H, D)] = sgm.sgm_autotune(self.hs[i], self.L[i], self.R[i], self.Dd[i])
+        for i, (W, H, D) in enumerate(self.specs):  # handles made before tuning pick it up here
+            self.hs[i].close()
+            self.hs[i] = sgm.Handle(W, H, D, p)
+        self.de = sum(W * H * D for W, H, D in self.specs)
+        self.device_bytes = sum(sum(sgm.sgm_scratch_bytes(W, H, D, p)[:1]) for W, H, D in self.specs)
+
+    def close(self):
+        for h in self.hs:
+            h.close()
+
+
+def batch_timings(torch, sgm, bs, steps, warmup):
+    st = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    batch_ms = timed(lambda: sgm.sgm_batch_compute(bs.hs, bs.L, bs.R, bs.Dd, bs.U, bs.V, st), steps)
+
+    def one_by_one():
+        for i in range(len(bs.specs)):
+            bs.hs[i].compute(bs.L[i], bs.R[i], bs.Dd[i], st)
+            bs.hs[i].uvmap(bs.Dd[i], bs.U[i], bs.V[i], st)
+    seq_ms = timed(one_by_one, max(1, steps // 4))
+    return batch_ms, seq_ms
+
+
+def batch_summary(torch, sgm, steps, warmup):
+    """The batched workload's value beside the same pairs launched one by one."""
+    bs = BatchSet(torch, sgm)
+    batch_ms, seq_ms = batch_timings(torch, sgm, bs, steps, warmup)
+    out = {"config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(bs.specs), "de_per_step": bs.de},
+           "value": bs.de / (batch_ms / 1e3) / 1e6, "unit": "MDE/s", "ms_per_step": batch_ms, "steps": steps,
+           "one_pair_per_launch": {"ms_per_step": seq_ms, "value": bs.de / (seq_ms / 1e3) / 1e6},
+           "device_bytes": bs.device_bytes,
+           "tuned_blocks_per_sm": {f"{k[0]}x{k[1]}d{k[2]}": v for k, v in bs.tuned.items()}}
+    bs.close()
+    return out
+
+
 def run_batch(args):
     """64 pairs of mixed size and disparity range (9x7 census, 8 paths,
     P1=8, P2=96, LR 1, 3x3 median, U/V maps): one graph-replayed batch call per
@@ -577,58 +803,19 @@ def run_batch(args):
 
     from paper_1807_06271_gb300 import sgm
     torch.cuda.set_device(0)
-    specs = batch_specs()
-    p = sgm.SgmParams(census_w=9, census_h=7, path_mask=0xFF, P1=8, P2=96, lr_tolerance=1, median_k=3)
-    hs, L, R, Dd, U, V, pairs = [], [], [], [], [], [], []
-    for i, (W, H, D) in enumerate(specs):
-        sc = scenes.ground_scene(W, H, D, seed=1807 + 3 + i, n_obstacles=3, dlo=D // 6, dhi=(D * 6) // 7,
-                                 texture="value", sigma=2.0, occlusion=0.05)
-        pairs.append((sc.left, sc.right, (D, 9, 7, 0xFF, 8, 96, 1, 3, True, 0)))
-        hs.append(sgm.Handle(W, H, D, p))
-        L.append(torch.from_numpy(sc.left).cuda())
-        R.append(torch.from_numpy(sc.right).cuda())
-        Dd.append(torch.empty((H, W), dtype=torch.uint8, device="cuda"))
-        U.append(torch.empty((D, W), dtype=torch.int16, device="cuda"))
-        V.append(torch.empty((H, D), dtype=torch.int16, device="cuda"))
-    tuned = {}
-    for i, (W, H, D) in enumerate(specs):
-        if (W, H, D) not in tuned:
-            tuned[(W, H, D)] = sgm.sgm_autotune(hs[i], L[i], R[i], Dd[i])
-    for i, (W, H, D) in enumerate(specs):  # handles made before tuning pick it up here
-        hs[i].close()
-        hs[i] = sgm.Handle(W, H, D, p)
-    de = sum(W * H * D for W, H, D in specs)
-    st = torch.cuda.current_stream()
-
-    def timed(fn, steps):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(steps):
-            fn()
-        e1.record(st)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
-
-    batch_ms = timed(lambda: sgm.sgm_batch_compute(hs, L, R, Dd, U, V, st), args.steps)
-
-    def one_by_one():
-        for i in range(len(specs)):
-            hs[i].compute(L[i], R[i], Dd[i], st)
-            hs[i].uvmap(Dd[i], U[i], V[i], st)
-    seq_ms = timed(one_by_one, max(1, args.steps // 4))
-    line = {"metric": "MDE/s", "value": de / (batch_ms / 1e3) / 1e6, "unit": "MDE/s", "n_gpus": 1,
+    bs = BatchSet(torch, sgm)
+    batch_ms, seq_ms = batch_timings(torch, sgm, bs, args.steps, args.warmup)
+    line = {"metric": "MDE/s", "value": bs.de / (batch_ms / 1e3) / 1e6, "unit": "MDE/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(specs),
-                       "de_per_step": de, "tuned_blocks_per_sm": {f"{k[0]}x{k[1]}d{k[2]}": v for k, v in tuned.items()}},
-            "one_pair_per_launch": {"ms_per_step": seq_ms, "value": de / (seq_ms / 1e3) / 1e6},
-            "cpu_baseline": None}
-    for h in hs:
-        h.close()
+            "config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(bs.specs),
+                       "de_per_step": bs.de,
+                       "tuned_blocks_per_sm": {f"{k[0]}x{k[1]}d{k[2]}": v for k, v in bs.tuned.items()}},
+            "one_pair_per_launch": {"ms_per_step": seq_ms, "value": bs.de / (seq_ms / 1e3) / 1e6},
+            "device_bytes": bs.device_bytes, "cpu_baseline": None}
+    pairs = bs.pairs
+    bs.close()
     if not args.no_cpu_baseline:
         # the oracle over the same 64 pairs, whole pairs spread over one process per host core
         pool = OraclePool()
@@ -640,28 +827,41 @@ def run_batch(args):
     return 0
 
 
-def run_serve(args):
+def serve_run(seconds):
     """8 cameras (4 x 640x480 D=64, 4 x 1280x720 D=128) with Poisson arrivals
     at 30 fps each, full path + U/V per frame, 4 GB device-memory budget."""
-    import torch
-
     from paper_1807_06271_gb300 import serving
-    torch.cuda.set_device(0)
     specs = serving.camera_streams()
     frames = serving.stream_frames(specs, per_stream=4)
     ex = serving.CudaExecutor(specs, frames)
     sch = serving.Scheduler(specs, ex, memory_budget=4 << 30)
     warm = serving.poisson_schedule(specs, duration_s=0.5, seed=1)
     serving.Scheduler(specs, ex, memory_budget=4 << 30).run(warm, speed=1.0)  # allocates slots, warms up
-    st = sch.run(serving.poisson_schedule(specs, duration_s=args.serve_seconds, seed=1807 + 4))
-    sm = st.summary()
+    st = sch.run(serving.poisson_schedule(specs, duration_s=seconds, seed=1807 + 4))
+    ex.close()
+    return specs, frames, st.summary()
+
+
+def serve_summary(torch, seconds):
+    _, _, sm = serve_run(seconds)
+    return {"config": {"workload": "serve-8cams-30fps-4GB", "seconds": seconds,
+                       "note": ("shortened to keep the default line within minutes; the workload's 60 s run is "
+                                "`bench.py --mode serve`") if seconds < 60 else "full 60 s run"},
+            "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "max_ms": sm["max_ms"], "frames": sm["frames"],
+            "mde_per_s": sm["mde_per_s"], "slots": sm["slots"], "device_bytes": sm["device_bytes"],
+            "max_queue": sm["max_queue"]}
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    specs, frames, sm = serve_run(args.serve_seconds)
     line = {"metric": "p99 latency", "value": sm["p99_ms"], "unit": "ms", "n_gpus": 1,
             "higher_is_better": False, "data": "synthetic",
             "config": {"workload": "serve-8cams-30fps-4GB", "seconds": args.serve_seconds},
             "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "max_ms": sm["max_ms"],
             "frames": sm["frames"], "mde_per_s": sm["mde_per_s"], "slots": sm["slots"],
             "device_bytes": sm["device_bytes"], "max_queue": sm["max_queue"], "cpu_baseline": None}
-    ex.close()
     if not args.no_cpu_baseline:
         # the oracle per camera type: one frame each, single thread, and the
         # frame rate with one frame per host core
@@ -704,7 +904,12 @@ def main(argv=None):
     ap.add_argument("--mode", choices=["frame", "batch", "serve"], default="frame",
                     help="frame: the headline single-pair line; batch: 64 mixed pairs per step; "
                          "serve: 8 Poisson camera streams")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the --mode serve run (the workload's 60 s)")
+    ap.add_argument("--line-serve-seconds", type=float, default=15.0,
+                    help="length of the serve run inside the default frame line's per_config")
+    ap.add_argument("--no-per-config", action="store_true",
+                    help="time only the headline workload (no per_config block)")
     ap.add_argument("--reference-seconds", type=float, default=120.0,
                     help="host time the reference arm's warm-up plus timed steps should take")
     args = ap.parse_args(argv)

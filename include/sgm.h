@@ -194,6 +194,18 @@ const char *sgm_status_string(int status);
 /* Sizes the handle was created with; any pointer may be NULL. */
 int sgm_get_shape(sgm_handle h, int *W, int *H, int *D, int *census_bits);
 
+/* Device memory, in bytes, that the library uses for W x H images with D
+ * disparities and `params` (checked as by sgm_create; the paper has no
+ * counterpart).  *handle_bytes: what sgm_create allocates (census codes, cost
+ * volume, one plane per enabled path, LR map, work-queue state), without the
+ * guard bytes of sgm_debug_canaries.  *host_staging_bytes: what the
+ * host-buffer entry points add on their first use (two staging slots of
+ * left, right, disp, U and V).  *static_bytes: the part of the fixed array
+ * that sgm_compute_static would use (it runs only when this is at most
+ * SGM_STATIC_SCRATCH_BYTES).  Any output pointer may be NULL.  No device call. */
+int sgm_scratch_bytes(int W, int H, int D, const sgm_params *params, size_t *handle_bytes,
+                      size_t *host_staging_bytes, size_t *static_bytes);
+
 /* Rectification (Sec. 3.1.1): later calls on h read the left and right
  * images through integer maps, I_rect(x, y) = I(map_x(x, y), map_y(x, y)),
  * inside the census kernel's tile load.  Each map is a device W x H uint16
@@ -288,6 +300,25 @@ int sgm_get_stage_times(sgm_handle h, float *ms, int *count, int n, int *n_stage
 /* Name of stage i ("census", "aggregate", ...), NULL when out of range. */
 const char *sgm_stage_name(int i);
 
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Operation mixes of sgm_probe_int_rate (the paper has no counterpart; these
+ * give the measured integer peak that the kernels' roofline is taken against). */
+#define SGM_PROBE_INT32_ADD_MIN 0  /* add.u32 and min.u32 in turn                  */
+#define SGM_PROBE_U16X2_MIN_ADD 1  /* min.u16x2 and add.u32 in turn: the packed
+                                      arithmetic of the aggregation (two 16-bit
+                                      operations per lane and instruction)          */
+#define SGM_PROBE_POPC_XOR 2       /* xor.b32 then popc.b32: the Hamming cost       */
+
+/* Times one launch of a probe kernel on the current device: 8 blocks of 256
+ * threads per SM, each thread running 8 independent chains of `iters` steps
+ * of the chosen two-operation mix (iters >= 8; about 20000 gives a launch of
+ * a few ms).  *lane_ops_per_s receives the instructions executed per second,
+ * counted per lane (a packed 16-bit instruction counts once); *ms (may be
+ * NULL) the launch's event time.  Synchronises the device; allocates and
+ * frees 256 bytes. */
+int sgm_probe_int_rate(int kind, int iters, double *lane_ops_per_s, float *ms);
+
 /* ---- no-allocation variant ------------------------------------------------ */
 
 /* Size in bytes of the device array that holds the scratch of
@@ -303,16 +334,21 @@ const char *sgm_stage_name(int i);
  * that must avoid the device synchronisation cudaFree implies.
  *   Arguments and checks as sgm_create + sgm_compute: left/right are device
  *   images of H rows of row_pitch bytes, disp is a device H x W byte map.
+ *   All three must be device (or managed) memory of one device, else
+ *   SGM_ERR_INVALID_ARG; the call runs on that device whichever is current,
+ *   and `stream` must belong to it.
  *   Scratch: census codes (2*W*H*4 bytes when census_w*census_h-1 <= 32, else
  *   2*W*H*8; none for SGM_COST_SAD), a cost volume and one plane per enabled
  *   path of W*H*Dp*e bytes each (Dp = D rounded up to 8 times a power of two:
  *   8, 16, 32, 64, 128 or 256; e = 1 for census, 2 for SAD), the aggregation's
- *   work-queue state (4224 bytes) and a W*H byte map, each rounded up to 256
- *   bytes.  A call that needs more than SGM_STATIC_SCRATCH_BYTES returns
+ *   work-queue state and status word (4228 bytes) and a W*H byte map, each
+ *   starting at a 256-byte boundary (sgm_scratch_bytes gives the total).  A
+ *   call that needs more than SGM_STATIC_SCRATCH_BYTES returns
  *   SGM_ERR_UNSUPPORTED before any GPU work (320x240 with D=64 and 4 paths
  *   needs about 25 MiB).
  *   The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.
+ *   device current, and so does the first call after the device's context was
+ *   made again (cudaDeviceReset); make those calls before any stream capture.
  *   All calls on a device share the one array and leave their data in it
  *   (nothing there needs to start at zero).  Calls whose work overlaps on the
  *   GPU (other streams, other host threads) race and corrupt each other's

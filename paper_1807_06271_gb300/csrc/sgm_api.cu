@@ -259,6 +259,23 @@ int sgm::compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right
 // Same host-side argument checks as sgm_create, for entry points without a handle.
 int sgm::validate_params(int W, int H, int D, const sgm_params *p) { return validate(W, H, D, p); }
 
+sgm::ScratchSizes sgm::scratch_sizes(int W, int H, int D, const sgm_params *p) {
+    const bool wide = p->cost == SGM_COST_SAD;
+    const int nbits = p->census_w * p->census_h - 1;
+    const size_t code_bytes = wide ? 0 : (nbits <= 32 ? 4 : 8);
+    const size_t eb = wide ? 2 : 1;  // bytes per cost / path cost
+    const size_t npx = (size_t)W * H, Dp = (size_t)padded_disparities(D);
+    const size_t npaths = (size_t)__builtin_popcount((unsigned)p->path_mask);
+    ScratchSizes s;
+    s.codes = 2 * npx * code_bytes;
+    s.cost = npx * Dp * eb;
+    s.job_state = kJobStateBytes + sizeof(unsigned);
+    s.planes = npaths * npx * Dp * eb;
+    s.disp_lr = npx;
+    s.staging_slot = 3 * npx + 2 * (size_t)D * W + 2 * (size_t)H * D;
+    return s;
+}
+
 extern "C" {
 
 const char *sgm_status_string(int status) {
@@ -305,18 +322,17 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
         const int v = atoi(env);
         if (v >= 1 && v <= 16) h->agg_blocks_per_sm = v;
     }
-    const size_t npx = (size_t)W * H;
-    const size_t eb = h->wide ? 2 : 1;  // bytes per cost / path cost
+    const ScratchSizes sz = scratch_sizes(W, H, D, params);
     h->canaries = g_canaries.load();
-    rc = h->wide ? SGM_OK : dev_alloc(h, &h->codes, 2 * npx * h->code_bytes);
-    if (rc == SGM_OK) rc = dev_alloc(h, &h->cost, npx * h->Dp * eb);
-    if (rc == SGM_OK) rc = dev_alloc(h, &h->job_counter, kJobStateBytes + sizeof(unsigned));
+    rc = h->wide ? SGM_OK : dev_alloc(h, &h->codes, sz.codes);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->cost, sz.cost);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->job_counter, sz.job_state);
     if (rc == SGM_OK) {
         h->dev_status = h->job_counter + kJobStateBytes / sizeof(unsigned);
         if (cudaMemset(h->dev_status, 0, sizeof(unsigned)) != cudaSuccess) rc = SGM_ERR_CUDA;
     }
-    if (rc == SGM_OK) rc = dev_alloc(h, &h->planes, (size_t)h->npaths * npx * h->Dp * eb);
-    if (rc == SGM_OK) rc = dev_alloc(h, &h->disp_lr, npx);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->planes, sz.planes);
+    if (rc == SGM_OK) rc = dev_alloc(h, &h->disp_lr, sz.disp_lr);
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
         rc = SGM_ERR_CUDA;
     if (rc == SGM_OK && (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -337,6 +353,17 @@ int sgm_destroy(sgm_handle h) {
     cudaDeviceSynchronize();
     batch_forget(h);
     free_handle(h);
+    return SGM_OK;
+}
+
+int sgm_scratch_bytes(int W, int H, int D, const sgm_params *params, size_t *handle_bytes,
+                      size_t *host_staging_bytes, size_t *static_bytes) {
+    const int rc = validate(W, H, D, params);
+    if (rc != SGM_OK) return rc;
+    const ScratchSizes sz = scratch_sizes(W, H, D, params);
+    if (handle_bytes) *handle_bytes = sz.handle();
+    if (host_staging_bytes) *host_staging_bytes = 2 * sz.staging_slot;
+    if (static_bytes) *static_bytes = static_scratch_bytes(sz);
     return SGM_OK;
 }
 

@@ -84,6 +84,30 @@ struct sgm_handle_s {
 
 namespace sgm {
 
+// Bytes of each device buffer of one pair.  sgm_create allocates each as its
+// own buffer, sgm_compute_static packs them into its fixed array, and
+// sgm_scratch_bytes reports them, all from this one computation.
+struct ScratchSizes {
+    size_t codes;         // census codes of both images (0 for SAD)
+    size_t cost;          // cost volume
+    size_t job_state;     // aggregation work-queue state plus the device status word
+    size_t planes;        // one plane per enabled path
+    size_t disp_lr;       // map after the LR check
+    size_t staging_slot;  // one host-path staging slot: left, right, disp, U, V
+    size_t handle() const { return codes + cost + job_state + planes + disp_lr; }
+};
+// Call only with parameters that passed validate_params.
+ScratchSizes scratch_sizes(int W, int H, int D, const sgm_params *p);
+
+// Where sgm_compute_static places each buffer in its fixed array: codes,
+// cost volume, planes, work-queue state and LR map in turn, each at a
+// 256-byte boundary; end is the number of bytes used.
+struct StaticLayout {
+    size_t codes, cost, planes, job_state, disp_lr, end;
+};
+StaticLayout static_layout(const ScratchSizes &sz);
+inline size_t static_scratch_bytes(const ScratchSizes &sz) { return static_layout(sz).end; }
+
 // One pair (and its U/V maps when umap and vmap are non-null) on stream s.
 int compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
                  uint16_t *umap, uint16_t *vmap, cudaStream_t s);

@@ -44,19 +44,14 @@ class StreamSpec:
 
 
 def slot_device_bytes(spec: StreamSpec) -> int:
-    """Device memory of one slot: census codes, cost volume, path planes,
-    LR map, the aggregation's work-queue state (4224 bytes) with the device
-    status word, and the slot's input/output buffers."""
-    npx = spec.W * spec.H
-    lanes = 1
-    while lanes * 8 < spec.D:
-        lanes *= 2
-    Dp = 8 * lanes
-    code_bytes = 4 if spec.census_w * spec.census_h - 1 <= 32 else 8
-    npaths = bin(spec.path_mask).count("1")
-    scratch = 2 * npx * code_bytes + npx * Dp + npaths * npx * Dp + npx + 4224 + 4
-    io = 2 * npx + npx + 2 * spec.D * spec.W + 2 * spec.H * spec.D
-    return scratch + 2 * io
+    """Device memory of one slot, as the library reports it: the handle's
+    scratch (census codes, cost volume, path planes, LR map, work-queue state)
+    plus the two staging slots of its pipelined host-buffer entry point."""
+    from . import sgm
+    p = sgm.SgmParams(census_w=spec.census_w, census_h=spec.census_h, path_mask=spec.path_mask,
+                      P1=spec.P1, P2=spec.P2, lr_tolerance=spec.lr_tolerance, median_k=spec.median_k)
+    handle, staging, _ = sgm.sgm_scratch_bytes(spec.W, spec.H, spec.D, p)
+    return handle + staging
 
 
 @dataclass

@@ -103,9 +103,16 @@ _SIGNATURES = {
     "sgm_debug_canaries": [_I],
     "sgm_debug_check_canaries": [_P],
     "sgm_debug_poke_canary": [_P, _I],
+    "sgm_scratch_bytes": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P],
+    "sgm_probe_int_rate": [_I, _I, _P, _P],
 }
 
 SGM_STATIC_SCRATCH_BYTES = 32 << 20
+
+# operation mixes of sgm_probe_int_rate
+SGM_PROBE_INT32_ADD_MIN = 0
+SGM_PROBE_U16X2_MIN_ADD = 1
+SGM_PROBE_POPC_XOR = 2
 
 
 def library_path() -> str:
@@ -403,15 +410,39 @@ def sgm_get_stage_times(h: Handle):
 
 def sgm_compute_static(W: int, H: int, D: int, params: SgmParams, left, right, disp, stream=None):
     """sgm_compute without a handle or any device allocation (scratch in a fixed
-    device array of SGM_STATIC_SCRATCH_BYTES per GPU).  Calls that overlap on
-    the GPU race on that array; the first call on a device must not be made
-    inside a stream capture."""
+    device array of SGM_STATIC_SCRATCH_BYTES per GPU).  left, right and disp
+    must live on one GPU; the call runs there.  Calls that overlap on the GPU
+    race on that array; the first call on a device must not be made inside a
+    stream capture."""
     shp = (H, params.row_pitch or W)
+    devs = {t.device for t in (left, right, disp) if t is not None and getattr(t, "is_cuda", False)}
+    if len(devs) > 1:
+        raise ValueError(f"sgm_compute_static: left, right and disp are on different devices {sorted(map(str, devs))}")
     p = params._c()
-    _check(load().sgm_compute_static(
-        W, H, D, ctypes.byref(p), _dev(left, ("uint8",), shp, "left"),
-        _dev(right, ("uint8",), shp, "right"), _dev(disp, ("uint8",), (H, W), "disp"),
-        _stream(stream)), "sgm_compute_static")
+    args = (W, H, D, ctypes.byref(p), _dev(left, ("uint8",), shp, "left"),
+            _dev(right, ("uint8",), shp, "right"), _dev(disp, ("uint8",), (H, W), "disp"))
+    import torch
+    with torch.cuda.device(left.device):
+        _check(load().sgm_compute_static(*args, _stream(stream)), "sgm_compute_static")
+
+
+def sgm_probe_int_rate(kind: int, iters: int = 20000):
+    """(lane instructions per second, launch ms) of the integer probe kernel
+    for one operation mix (SGM_PROBE_*) on the current device."""
+    r, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().sgm_probe_int_rate(kind, iters, ctypes.byref(r), ctypes.byref(ms)), "sgm_probe_int_rate")
+    return r.value, ms.value
+
+
+def sgm_scratch_bytes(W: int, H: int, D: int, params: SgmParams):
+    """(handle_bytes, host_staging_bytes, static_bytes): the device memory
+    sgm_create allocates, what the host-buffer entry points add, and what
+    sgm_compute_static would use of its fixed array (no device call)."""
+    p = params._c()
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().sgm_scratch_bytes(W, H, D, ctypes.byref(p), ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c)), "sgm_scratch_bytes")
+    return a.value, b.value, c.value
 
 
 def uvmap_postprocess(h: Handle, umap, vmap, u_threshold: int, v_threshold: int, u_roi=None,

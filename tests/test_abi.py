@@ -187,3 +187,64 @@ def test_static_entry_point_checks_before_any_device_call():
     assert lib.sgm_compute_static(10, 10, 16, ctypes.byref(good), None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_compute_static(10, 10, 16, None, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
     assert lib.sgm_debug_fail_alloc(-1) == sgm.SGM_ERR_INVALID_ARG
+
+
+def test_static_entry_point_rejects_memory_that_is_not_on_a_device():
+    """Host buffers (or, on a machine without a GPU, any buffer) are not device
+    memory of one device: SGM_ERR_INVALID_ARG, and nothing is launched."""
+    lib = sgm.load()
+    good = sgm.SgmParams(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_4)._c()
+    img = (ctypes.c_uint8 * (32 * 16))()
+    out = (ctypes.c_uint8 * (32 * 16))()
+    rc = lib.sgm_compute_static(32, 16, 16, ctypes.byref(good), ctypes.addressof(img), ctypes.addressof(img),
+                                ctypes.addressof(out), None)
+    assert rc == sgm.SGM_ERR_INVALID_ARG
+
+
+def _expected_bytes(W, H, D, cw, ch, mask, cost):
+    """Scratch sizes written out from the layout the header documents."""
+    lanes = 1
+    while 8 * lanes < D:
+        lanes *= 2
+    Dp = 8 * lanes
+    e = 2 if cost == sgm.SGM_COST_SAD else 1
+    code = 0 if cost == sgm.SGM_COST_SAD else (4 if cw * ch - 1 <= 32 else 8)
+    npx = W * H
+    npaths = bin(mask).count("1")
+    parts = [2 * npx * code, npx * Dp * e, npaths * npx * Dp * e, 4224 + 4, npx]
+    handle = sum(parts)
+    staging = 2 * (3 * npx + 2 * D * W + 2 * H * D)
+    at = 0
+    for i, b in enumerate((parts[0], parts[1], parts[2], parts[3])):
+        at = (at + b + 255) // 256 * 256
+    static = at + npx
+    return handle, staging, static
+
+
+@pytest.mark.parametrize("W,H,D,cw,ch,mask,cost", [
+    (320, 240, 64, 5, 5, sgm.SGM_PATHS_4, sgm.SGM_COST_CENSUS),
+    (1242, 375, 128, 9, 7, sgm.SGM_PATHS_8, sgm.SGM_COST_CENSUS),
+    (640, 360, 60, 5, 5, sgm.SGM_PATHS_STREAM4, sgm.SGM_COST_SAD),
+    (17, 3, 255, 3, 3, 0x01, sgm.SGM_COST_CENSUS),
+])
+def test_scratch_bytes_follow_the_documented_layout(W, H, D, cw, ch, mask, cost):
+    p = sgm.SgmParams(census_w=cw, census_h=ch, path_mask=mask, P1=8 if cost == 0 else 200,
+                      P2=32 if cost == 0 else 800, cost=cost)
+    assert sgm.sgm_scratch_bytes(W, H, D, p) == _expected_bytes(W, H, D, cw, ch, mask, cost)
+
+
+def test_scratch_bytes_checks_its_arguments():
+    lib = sgm.load()
+    bad = sgm.SgmParams(census_w=4)._c()
+    assert lib.sgm_scratch_bytes(10, 10, 16, ctypes.byref(bad), None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_scratch_bytes(10, 10, 16, None, None, None, None) == sgm.SGM_ERR_INVALID_ARG
+    big = sgm.SgmParams(census_w=9, census_h=9)._c()
+    assert lib.sgm_scratch_bytes(10, 10, 16, ctypes.byref(big), None, None, None) == sgm.SGM_ERR_UNSUPPORTED
+
+
+def test_static_limit_follows_the_scratch_query():
+    """The 320x240, D=64, 4-path workload fits the fixed array; the KITTI-shaped one does not."""
+    small = sgm.SgmParams(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_4, P1=4, P2=24)
+    big = sgm.SgmParams(census_w=9, census_h=7, path_mask=sgm.SGM_PATHS_8, P1=8, P2=96)
+    assert sgm.sgm_scratch_bytes(320, 240, 64, small)[2] <= sgm.SGM_STATIC_SCRATCH_BYTES
+    assert sgm.sgm_scratch_bytes(1242, 375, 128, big)[2] > sgm.SGM_STATIC_SCRATCH_BYTES

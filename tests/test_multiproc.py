@@ -96,15 +96,43 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 
 
 def test_roofline_host_arithmetic():
-    """Ops per estimate (7 per path plus the cost), the INT32 issue peak, and
-    traffic taken from a profile summary only when its source digest matches."""
+    """Ops per estimate of the aggregation kernel (7 per path), of the cost
+    and of the whole path (72 for the 8-path 9x7 workload, 37 for the 4-path
+    5x5 ones, as the survey counts them), the HBM bytes the path must move,
+    and the path roofline as min(integer bound, HBM bound)."""
     import bench
     from paper_1807_06271_gb300 import scenes
-    ops = bench.workload_ops(scenes.KITTI_1242)          # 8 paths, 62-bit codes
-    assert ops["per_de"] == 7 * 8 + 5 == 61
-    assert bench.workload_ops(scenes.SMALL_320)["per_de"] == 7 * 4 + 2 == 30   # 4 paths, 24-bit codes
-    assert bench.workload_ops(scenes.PAPER_640_SAD)["per_de"] == 7 * 4 + 2 * 5 + 5  # 5x5 SAD
-    assert abs(bench.int_peak_tops() - 152 * 128 * 2.07e9 / 1e12) < 1e-9
+    assert bench.aggregation_ops(scenes.KITTI_1242)["per_de"] == 7 * 8 == 56
+    assert bench.aggregation_ops(scenes.SMALL_320)["per_de"] == 28
+    assert bench.cost_ops(scenes.KITTI_1242) == 5 and bench.cost_ops(scenes.SMALL_320) == 2
+    assert bench.cost_ops(scenes.PAPER_640_SAD) == 2 * 5 + 5
+    assert bench.popc_per_de(scenes.KITTI_1242) == 2 and bench.popc_per_de(scenes.PAPER_640_SAD) == 0
+    assert bench.path_ops(scenes.KITTI_1242) == 72
+    assert bench.path_ops(scenes.SMALL_320) == bench.path_ops(scenes.HD_1280) == 37
+    # both ways along the scanlines: one 16-bit partial written and read (4 B);
+    # the paper's streaming set is causal in one sweep: images in, map out
+    assert bench.path_hbm_bytes_per_de(scenes.KITTI_1242) == 4.0
+    assert bench.path_hbm_bytes_per_de(scenes.SMALL_320) == 4.0
+    assert bench.path_hbm_bytes_per_de(scenes.PAPER_640) == 3.0 / 60
+    peaks = {"int32_tops": 40.0, "u16x2_tops": 80.0, "popc_tops": 5.0}
+    r = bench.path_roofline(scenes.KITTI_1242, 200000.0, peaks, 6700.0)
+    assert r["int_bound_mde_s"] == 40e12 / 72 / 1e6 and r["hbm_bound_mde_s"] == 6700e9 / 4 / 1e6
+    assert r["bound"] == "alu" and abs(r["frac"] - 200000.0 / (40e12 / 72 / 1e6)) < 1e-12
+    k = bench.kernel_rooflines(scenes.KITTI_1242, {"aggregate": (1.0, 10), "cost": (0.3, 10), "wta_lr": (0.8, 10)},
+                               peaks, 6700.0)
+    de = 1242 * 375 * 128
+    assert abs(k["aggregate"]["achieved_tops"] - 56 * de / 1e-4 / 1e12) < 1e-6
+    assert abs(k["cost"]["achieved_tpopc"] - 2 * de / 3e-5 / 1e12) < 1e-6
+    assert k["wta_lr"]["bytes"] == 1242 * 375 * (8 * 128 + 1)
+
+
+def test_hbm_peak_comes_from_the_measured_file(tmp_path, monkeypatch):
+    import json
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm_gbs() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6700.8}))
+    assert bench.measured_hbm_gbs() == (6700.8, "measured")
 
 
 def test_profiled_traffic_needs_the_current_source(tmp_path, monkeypatch):

@@ -4,7 +4,8 @@ sgm_compute_static serves callers that cannot call cudaMalloc (a hard-deadline
 camera loop, a host framework that owns all device memory); it keeps its
 scratch in one fixed device array per GPU.  Its results must equal
 sgm_compute's bit for bit, also on consecutive calls that reuse the array
-with different image sizes and parameters.  This file is collected last."""
+with different image sizes and parameters, and a call must allocate no
+device memory.  This file is collected last."""
 import ctypes
 
 import numpy as np
@@ -63,3 +64,66 @@ def test_static_rejects_scratch_beyond_its_maximum():
     pc = p._c()
     assert sgm.load().sgm_compute_static(w.W, w.H, w.D, ctypes.byref(pc), None, None, None,
                                          None) == sgm.SGM_ERR_INVALID_ARG
+
+
+def test_static_allocates_nothing():
+    """With the library's next device allocation set to fail, the static call
+    still succeeds, and the device's free memory is the same before and after
+    it (outputs and inputs are allocated up front)."""
+    W, H, D = 320, 240, 64
+    s = scenes.boxes_scene(W, H, D, seed=97, n_boxes=3, dlo=2, dhi=D - 2)
+    p = sgm.SgmParams(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_4, P1=4, P2=24,
+                      lr_tolerance=1, median_k=5)
+    left = torch.from_numpy(s.left).cuda()
+    right = torch.from_numpy(s.right).cuda()
+    got = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    sgm.sgm_compute_static(W, H, D, p, left, right, got)  # first call: device address lookup
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    sgm.sgm_debug_fail_alloc(1)
+    try:
+        for _ in range(2):
+            sgm.sgm_compute_static(W, H, D, p, left, right, got)
+        torch.cuda.synchronize()
+    finally:
+        sgm.sgm_debug_fail_alloc(0)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ref = oracle.sgm(s.left, s.right, D, 5, 5, p.path_mask, p.P1, p.P2, p.lr_tolerance, p.median_k, uv=False)
+    assert np.array_equal(got.cpu().numpy(), ref["disp"])
+
+
+def test_static_without_median_on_a_side_stream():
+    """median_k = 1 (the LR map is copied out) and a tolerance of 0, on a
+    non-default stream, twice in a row: equal to the handle path and the oracle."""
+    W, H, D = 256, 200, 48
+    p = sgm.SgmParams(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_8, P1=8, P2=32,
+                      lr_tolerance=0, median_k=1)
+    st = torch.cuda.Stream()
+    for seed in (101, 102):
+        s = scenes.boxes_scene(W, H, D, seed=seed, n_boxes=3, dlo=2, dhi=D - 2)
+        left = torch.from_numpy(s.left).cuda()
+        right = torch.from_numpy(s.right).cuda()
+        want = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        with sgm.Handle(W, H, D, p) as h:
+            h.compute(left, right, want)
+        torch.cuda.synchronize()
+        got = torch.full((H, W), 7, dtype=torch.uint8, device="cuda")
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            sgm.sgm_compute_static(W, H, D, p, left, right, got, st)
+        st.synchronize()
+        assert np.array_equal(got.cpu().numpy(), want.cpu().numpy())
+        ref = oracle.sgm(s.left, s.right, D, 5, 5, p.path_mask, p.P1, p.P2, 0, 1, uv=False)
+        assert np.array_equal(got.cpu().numpy(), ref["disp"])
+
+
+def test_static_rejects_a_host_buffer():
+    W, H, D = 64, 32, 16
+    p = sgm.SgmParams(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_4)
+    img = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    host = torch.zeros((H, W), dtype=torch.uint8).pin_memory()
+    pc = p._c()
+    rc = sgm.load().sgm_compute_static(W, H, D, ctypes.byref(pc), img.data_ptr(), img.data_ptr(),
+                                       host.data_ptr(), None)
+    assert rc == sgm.SGM_ERR_INVALID_ARG

@@ -180,11 +180,42 @@ int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
                       const uint8_t *const *right, uint8_t *const *disp,
                       uint16_t *const *umap, uint16_t *const *vmap, void *stream);
 
+/* Path schedules: how the aggregation of Eq. 2 is organised on the GPU.
+ *   PLANES: every enabled direction is cut into independent scanlines that
+ *     run concurrently over a materialised cost volume and write one plane
+ *     per direction; a second kernel sums the planes and takes both winners
+ *     and the LR check.  Any path set, D and cost.
+ *   SWEEP: the paper's streaming organisation (Sec. 3.1.3, Fig. 2): one
+ *     top-down pass in which the 0, 45, 90 and 135 degree paths of a row
+ *     continue from the row above, with the matching cost, S, both winners
+ *     and the LR check fused, so neither costs nor S reach memory.  Census
+ *     cost, D <= 128, path masks within SGM_PATHS_STREAM4 (0x55); one warp per
+ *     image row, rows_per_cta rows (2..8) per thread block, all blocks
+ *     resident at once.
+ *   AUTO: what sgm_autotune chose for this shape, else PLANES.
+ * Both give the same disparities bit for bit. */
+#define SGM_SCHEDULE_AUTO 0
+#define SGM_SCHEDULE_PLANES 1
+#define SGM_SCHEDULE_SWEEP 2
+
+/* Selects the schedule of later calls on h (rows_per_cta is used by SWEEP
+ * only).  SGM_ERR_UNSUPPORTED when h's parameters rule the sweep out or its
+ * blocks cannot all be resident on the device; SGM_ERR_INVALID_ARG for an
+ * unknown schedule or rows_per_cta outside 2..8.  h is unchanged on error. */
+int sgm_set_schedule(sgm_handle h, int schedule, int rows_per_cta);
+
+/* The schedule in use (SGM_SCHEDULE_PLANES or SGM_SCHEDULE_SWEEP, never AUTO)
+ * and the sweep's rows per thread block; either pointer may be NULL. */
+int sgm_get_schedule(sgm_handle h, int *schedule, int *rows_per_cta);
+
 /* Autotuner: times the pipeline on this pair (device pointers as for
- * sgm_compute; disp is overwritten) with 1, 2, 3, 4 and 6 resident blocks per
- * SM for the aggregation kernel and keeps the fastest for h and for handles
- * created later in this process with the same W, H, D, path mask, census
- * window and P2.  Synchronises `stream`.  *best_blocks_per_sm may be NULL. */
+ * sgm_compute; disp is overwritten) with the PLANES schedule at 1, 2, 3, 4
+ * and 6 resident aggregation blocks per SM and, where h can run it, the SWEEP
+ * schedule at 2, 4 and 8 rows per block; keeps the fastest for h and for
+ * handles created later in this process with the same W, H, D, path mask,
+ * cost, window and P2.  *best_blocks_per_sm (may be NULL) receives the best
+ * PLANES setting; sgm_get_schedule tells which schedule won.  Synchronises
+ * `stream`. */
 int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
                  void *stream, int *best_blocks_per_sm);
 
@@ -252,8 +283,10 @@ int sgm_set_cost_kernel(sgm_handle h, int kernel);
 
 /* Waits for the device, then returns SGM_ERR_TIMEOUT if a kernel of h gave up
  * a bounded device-side wait since the previous call (the tensor-core cost
- * kernel waits about one second at most for its matrix product; it then
- * writes no costs for that segment), else SGM_OK.  Clears the record. */
+ * kernel waits about one second at most for its matrix product, and then
+ * writes no costs for that segment; the fused sweep waits about one second at
+ * most for the row above it, and then leaves that call's disparity map
+ * unfinished), else SGM_OK.  Clears the record. */
 int sgm_device_status(sgm_handle h);
 
 /* Test of the bounded device waits: runs the census and the tensor-core cost

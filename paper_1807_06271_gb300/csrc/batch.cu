@@ -28,15 +28,16 @@ std::vector<BatchGraph> g_graphs;
 unsigned long long g_clock = 0;
 
 struct TuneKey {
-    int W, H, D, mask, cw, ch, P2;
+    int W, H, D, mask, cw, ch, P2, cost;
     bool operator==(const TuneKey &o) const {
-        return W == o.W && H == o.H && D == o.D && mask == o.mask && cw == o.cw && ch == o.ch && P2 == o.P2;
+        return W == o.W && H == o.H && D == o.D && mask == o.mask && cw == o.cw && ch == o.ch && P2 == o.P2 &&
+               cost == o.cost;
     }
 };
-std::vector<std::pair<TuneKey, int>> g_tuned;
+std::vector<std::pair<TuneKey, sgm::Tuning>> g_tuned;
 
 TuneKey tune_key(const sgm_handle_s *h) {
-    return {h->W, h->H, h->D, h->p.path_mask, h->p.census_w, h->p.census_h, h->p.P2};
+    return {h->W, h->H, h->D, h->p.path_mask, h->p.census_w, h->p.census_h, h->p.P2, h->p.cost};
 }
 
 void drop(BatchGraph &g) {
@@ -80,12 +81,12 @@ void sgm::batch_forget(sgm_handle_s *h) {
                    g_graphs.end());
 }
 
-int sgm::tuned_blocks_per_sm(const sgm_handle_s *h) {
+sgm::Tuning sgm::tuned_for(const sgm_handle_s *h) {
     std::lock_guard<std::mutex> lock(g_mu);
     const TuneKey k = tune_key(h);
     for (auto &e : g_tuned)
         if (e.first == k) return e.second;
-    return 0;
+    return Tuning{0, SGM_SCHEDULE_PLANES, 4};
 }
 
 extern "C" int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
@@ -113,7 +114,7 @@ extern "C" int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *con
         rc = run_forked(n, hs, left, right, disp, umap, vmap, s);
     } else {
         BatchKey key;
-        key.v.reserve(7 * n);
+        key.v.reserve(8 * n);
         for (int i = 0; i < n; i++) {
             key.v.push_back(hs[i]);
             key.v.push_back(left[i]);
@@ -122,6 +123,7 @@ extern "C" int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *con
             key.v.push_back(umap && vmap ? (const void *)umap[i] : nullptr);
             key.v.push_back(umap && vmap ? (const void *)vmap[i] : nullptr);
             key.v.push_back((const void *)(intptr_t)hs[i]->agg_blocks_per_sm);
+            key.v.push_back((const void *)(intptr_t)(hs[i]->schedule * 64 + hs[i]->sweep_rows));
         }
         std::lock_guard<std::mutex> lock(g_mu);
         BatchGraph *hit = nullptr;
@@ -180,13 +182,25 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
     int rc = SGM_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SGM_ERR_CUDA;
     const int saved = h->agg_blocks_per_sm, saved_timing = h->timing;
+    const int saved_schedule = h->schedule, saved_rows = h->sweep_rows;
     h->timing = 0;
-    int best = saved;
-    float best_ms = 1e30f;
-    const int candidates[] = {1, 2, 3, 4, 6};
-    for (int c : candidates) {
+    // candidates: the plane schedule at each resident-block count, then the
+    // fused sweep at each rows-per-CTA count it can run with
+    struct Cand {
+        int schedule, param;
+    };
+    std::vector<Cand> cands;
+    for (int c : {1, 2, 3, 4, 6}) cands.push_back({SGM_SCHEDULE_PLANES, c});
+    for (int r : {2, 4, 8})
+        if (sgm::sweep_feasible(h, r) == SGM_OK) cands.push_back({SGM_SCHEDULE_SWEEP, r});
+    int best_bps = saved;
+    Cand best{saved_schedule, saved_schedule == SGM_SCHEDULE_SWEEP ? saved_rows : saved};
+    float best_ms = 1e30f, best_planes_ms = 1e30f;
+    for (const Cand &c : cands) {
         if (rc != SGM_OK) break;
-        h->agg_blocks_per_sm = c;
+        h->schedule = c.schedule;
+        if (c.schedule == SGM_SCHEDULE_SWEEP) h->sweep_rows = c.param;
+        else h->agg_blocks_per_sm = c.param;
         for (int w = 0; w < 2 && rc == SGM_OK; w++)
             rc = sgm::compute_pair(h, left, right, disp, nullptr, nullptr, s);
         if (rc != SGM_OK) break;
@@ -197,24 +211,38 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
         if (rc == SGM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
             rc = SGM_ERR_CUDA;
+        if (rc == SGM_OK && c.schedule == SGM_SCHEDULE_PLANES && ms < best_planes_ms) {
+            best_planes_ms = ms;
+            best_bps = c.param;
+        }
         if (rc == SGM_OK && ms < best_ms) {
             best_ms = ms;
             best = c;
         }
     }
     h->timing = saved_timing;
-    h->agg_blocks_per_sm = rc == SGM_OK ? best : saved;
+    if (rc == SGM_OK) {
+        h->agg_blocks_per_sm = best_bps;
+        h->schedule = best.schedule;
+        h->sweep_rows = best.schedule == SGM_SCHEDULE_SWEEP ? best.param : saved_rows;
+    } else {
+        h->agg_blocks_per_sm = saved;
+        h->schedule = saved_schedule;
+        h->sweep_rows = saved_rows;
+    }
+    sgm::batch_forget(h);
     if (rc == SGM_OK) {
         std::lock_guard<std::mutex> lock(g_mu);
         const TuneKey k = tune_key(h);
+        const sgm::Tuning t{best_bps, h->schedule, h->sweep_rows};
         bool found = false;
         for (auto &e : g_tuned)
             if (e.first == k) {
-                e.second = best;
+                e.second = t;
                 found = true;
             }
-        if (!found) g_tuned.push_back({k, best});
-        if (best_blocks_per_sm) *best_blocks_per_sm = best;
+        if (!found) g_tuned.push_back({k, t});
+        if (best_blocks_per_sm) *best_blocks_per_sm = best_bps;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -17,13 +17,13 @@ namespace {
 
 constexpr int kTimingRing = 1024;
 
-const char *const kStageNames[kNumStages] = {"census", "cost", "aggregate", "wta_lr", "median", "uvmap"};
+const char *const kStageNames[kNumStages] = {"census", "cost", "aggregate", "wta_lr", "median", "uvmap", "sweep"};
 // NVTX push/pop range around each stage's launches (host side; a tool attached
 // to the process can select kernels by range, e.g. ncu --nvtx --nvtx-include
 // "sgm:aggregate/").  Stage ranges are not nested in a per-pair range, so they
 // match at the top level of an application that opens none itself.
 const char *const kStageRanges[kNumStages] = {"sgm:census", "sgm:cost", "sgm:aggregate",
-                                              "sgm:wta_lr", "sgm:median", "sgm:uvmap"};
+                                              "sgm:wta_lr", "sgm:median", "sgm:uvmap", "sgm:sweep"};
 
 int validate(int W, int H, int D, const sgm_params *p) {
     if (!p || W < 1 || H < 1 || D < 1) return SGM_ERR_INVALID_ARG;
@@ -170,11 +170,27 @@ int run_median(sgm_handle_s *h, uint8_t *disp, cudaStream_t s) {
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
 
+// The fused streaming sweep (cost, paths, both winners, LR check) into h->disp_lr.
+int run_sweep(sgm_handle_s *h, uint8_t *dbg_left, uint8_t *dbg_right, cudaStream_t s) {
+    TimingRecord *t = stage_begin(h, kStageSweep, s);
+    cudaError_t e = launch_sweep(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->p.P1, h->p.P2,
+                                 h->p.path_mask, h->p.lr_tolerance, h->disp_lr, dbg_left, dbg_right,
+                                 h->sweep_scratch, h->dev_status, h->sweep_rows, s);
+    stage_end(h, t, s);
+    return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
+}
+
 int compute_on(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uint8_t *disp,
                cudaStream_t s) {
-    int rc = run_matching(h, left, right, s);
-    if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
-    if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, nullptr, s);
+    int rc;
+    if (h->schedule == SGM_SCHEDULE_SWEEP) {
+        rc = run_census(h, left, right, s);
+        if (rc == SGM_OK) rc = run_sweep(h, nullptr, nullptr, s);
+    } else {
+        rc = run_matching(h, left, right, s);
+        if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
+        if (rc == SGM_OK) rc = run_wta(h, nullptr, nullptr, nullptr, s);
+    }
     if (rc == SGM_OK) rc = run_median(h, disp, s);
     return rc;
 }
@@ -272,8 +288,17 @@ sgm::ScratchSizes sgm::scratch_sizes(int W, int H, int D, const sgm_params *p) {
     s.job_state = kJobStateBytes + sizeof(unsigned);
     s.planes = npaths * npx * Dp * eb;
     s.disp_lr = npx;
+    s.sweep = sweep_supported(D, p->path_mask, (int)code_bytes) ? sweep_scratch_bytes(W, H, D, kSweepMinRows) : 0;
     s.staging_slot = 3 * npx + 2 * (size_t)D * W + 2 * (size_t)H * D;
     return s;
+}
+
+int sgm::sweep_feasible(const sgm_handle_s *h, int rows) {
+    if (!h->sweep_scratch || !sweep_supported(h->D, h->p.path_mask, h->code_bytes)) return SGM_ERR_UNSUPPORTED;
+    if (rows < kSweepMinRows || rows > 8) return SGM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return SGM_ERR_CUDA;
+    return sweep_fits(h->H, h->D, h->code_bytes, rows) ? SGM_OK : SGM_ERR_UNSUPPORTED;
 }
 
 extern "C" {
@@ -316,8 +341,14 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
         if ((params->path_mask >> r) & 1) h->path_of_plane[h->npaths++] = r;
     h->Dp = padded_disparities(D);
     h->agg_blocks_per_sm = 3;  // 12 resident warps per SM (fastest on 1242 x 375, D = 128)
-    const int tuned = tuned_blocks_per_sm(h);
-    if (tuned > 0) h->agg_blocks_per_sm = tuned;
+    h->schedule = SGM_SCHEDULE_PLANES;
+    h->sweep_rows = 4;
+    const Tuning tuned = tuned_for(h);
+    if (tuned.blocks_per_sm > 0) {
+        h->agg_blocks_per_sm = tuned.blocks_per_sm;
+        h->schedule = tuned.schedule;
+        h->sweep_rows = tuned.sweep_rows;
+    }
     if (const char *env = getenv("SGM_AGG_BLOCKS_PER_SM")) {  // tuning override
         const int v = atoi(env);
         if (v >= 1 && v <= 16) h->agg_blocks_per_sm = v;
@@ -333,6 +364,9 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
     }
     if (rc == SGM_OK) rc = dev_alloc(h, &h->planes, sz.planes);
     if (rc == SGM_OK) rc = dev_alloc(h, &h->disp_lr, sz.disp_lr);
+    if (rc == SGM_OK && sz.sweep) rc = dev_alloc(h, &h->sweep_scratch, sz.sweep);
+    if (rc == SGM_OK && h->schedule == SGM_SCHEDULE_SWEEP && sweep_feasible(h, h->sweep_rows) != SGM_OK)
+        h->schedule = SGM_SCHEDULE_PLANES;
     if (rc == SGM_OK && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
         rc = SGM_ERR_CUDA;
     if (rc == SGM_OK && (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -677,9 +711,15 @@ int sgm_debug_raw(sgm_handle h, const uint8_t *left, const uint8_t *right, uint8
     DeviceGuard g(h->device);
     if (!g.ok) return SGM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = run_matching(h, left, right, s);
-    if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
-    if (rc == SGM_OK) rc = run_wta(h, disp_left, disp_right, nullptr, s);
+    int rc;
+    if (h->schedule == SGM_SCHEDULE_SWEEP) {
+        rc = run_census(h, left, right, s);
+        if (rc == SGM_OK) rc = run_sweep(h, disp_left, disp_right, s);
+    } else {
+        rc = run_matching(h, left, right, s);
+        if (rc == SGM_OK) rc = run_aggregate(h, -1, s);
+        if (rc == SGM_OK) rc = run_wta(h, disp_left, disp_right, nullptr, s);
+    }
     if (rc == SGM_OK && disp_lr &&
         cudaMemcpyAsync(disp_lr, h->disp_lr, (size_t)h->W * h->H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         rc = SGM_ERR_CUDA;
@@ -693,6 +733,32 @@ int sgm_set_rectification(sgm_handle h, const uint16_t *left_x, const uint16_t *
     if (set != 0 && set != 4) return SGM_ERR_INVALID_ARG;
     h->rect = {left_x, left_y, right_x, right_y};
     batch_forget(h);  // captured graphs hold the previous census launch
+    return SGM_OK;
+}
+
+int sgm_set_schedule(sgm_handle h, int schedule, int rows_per_cta) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    if (schedule == SGM_SCHEDULE_AUTO) {
+        const Tuning t = tuned_for(h);
+        schedule = t.blocks_per_sm > 0 ? t.schedule : SGM_SCHEDULE_PLANES;
+        rows_per_cta = t.blocks_per_sm > 0 ? t.sweep_rows : h->sweep_rows;
+        if (schedule == SGM_SCHEDULE_SWEEP && sweep_feasible(h, rows_per_cta) != SGM_OK) schedule = SGM_SCHEDULE_PLANES;
+    } else if (schedule == SGM_SCHEDULE_SWEEP) {
+        const int rc = sweep_feasible(h, rows_per_cta);
+        if (rc != SGM_OK) return rc;
+    } else if (schedule != SGM_SCHEDULE_PLANES) {
+        return SGM_ERR_INVALID_ARG;
+    }
+    h->schedule = schedule;
+    if (schedule == SGM_SCHEDULE_SWEEP) h->sweep_rows = rows_per_cta;
+    batch_forget(h);  // captured graphs hold the previous schedule's launches
+    return SGM_OK;
+}
+
+int sgm_get_schedule(sgm_handle h, int *schedule, int *rows_per_cta) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    if (schedule) *schedule = h->schedule;
+    if (rows_per_cta) *rows_per_cta = h->sweep_rows;
     return SGM_OK;
 }
 

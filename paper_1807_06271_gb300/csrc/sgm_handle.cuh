@@ -16,7 +16,7 @@ struct IoSlot {
     cudaEvent_t in_ready, computed, done;
 };
 
-enum Stage { kStageCensus = 0, kStageCost, kStageAggregate, kStageWta, kStageMedian, kStageUv, kNumStages };
+enum Stage { kStageCensus = 0, kStageCost, kStageAggregate, kStageWta, kStageMedian, kStageUv, kStageSweep, kNumStages };
 
 struct TimingRecord {
     int stage;
@@ -62,6 +62,9 @@ struct sgm_handle_s {
     unsigned *dev_status;   // bit 0: a bounded device wait gave up (one word after the work-queue state)
     int cost_kernel;        // SGM_COST_KERNEL_* of the census cost
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
+    int schedule;           // SGM_SCHEDULE_PLANES or SGM_SCHEDULE_SWEEP (resolved, never AUTO)
+    int sweep_rows;         // rows (warps) per CTA of the fused sweep
+    void *sweep_scratch;    // global rings, counters and right map of the fused sweep (null when unsupported)
     sgm::RectMaps rect;     // caller-owned rectification maps, or all null
 
     // device staging of the host-pointer entry points, allocated on first use:
@@ -93,8 +96,9 @@ struct ScratchSizes {
     size_t job_state;     // aggregation work-queue state plus the device status word
     size_t planes;        // one plane per enabled path
     size_t disp_lr;       // map after the LR check
+    size_t sweep;         // fused streaming sweep (0 when the path set or D rules it out)
     size_t staging_slot;  // one host-path staging slot: left, right, disp, U, V
-    size_t handle() const { return codes + cost + job_state + planes + disp_lr; }
+    size_t handle() const { return codes + cost + job_state + planes + disp_lr + sweep; }
 };
 // Call only with parameters that passed validate_params.
 ScratchSizes scratch_sizes(int W, int H, int D, const sgm_params *p);
@@ -113,7 +117,15 @@ int compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uin
                  uint16_t *umap, uint16_t *vmap, cudaStream_t s);
 // Drops cached batch graphs that use h (called before h is freed).
 void batch_forget(sgm_handle_s *h);
-// Aggregation blocks per SM chosen by sgm_autotune for h's shape, or 0.
-int tuned_blocks_per_sm(const sgm_handle_s *h);
+// What sgm_autotune chose for h's shape: aggregation blocks per SM (0: not
+// tuned), and the schedule with its rows per CTA.
+struct Tuning {
+    int blocks_per_sm, schedule, sweep_rows;
+};
+Tuning tuned_for(const sgm_handle_s *h);
+// Rows per CTA the fused sweep's scratch is sized for (the smallest it runs with).
+constexpr int kSweepMinRows = 2;
+// SGM_OK when h can run the fused sweep with `rows` rows per CTA on its device.
+int sweep_feasible(const sgm_handle_s *h, int rows);
 
 }  // namespace sgm

@@ -168,4 +168,18 @@ int validate_params(int W, int H, int D, const sgm_params *p);
 cudaError_t launch_uvmap(const uint8_t *disp, int W, int H, int D, uint16_t *umap, uint16_t *vmap,
                          cudaStream_t s);
 
+// The paper's streaming set in one top-down sweep with the cost, the paths,
+// both winners and the LR check fused (sweep.cu): census codes (code_bytes 4
+// or 8) of both images in, the checked map disp_lr out (dbg_left/dbg_right,
+// optional, receive the raw maps).  Supported for D <= 128 and path masks
+// within 0x55.  scratch: sweep_scratch_bytes(W, H, D, rows_per_cta) bytes.
+// A bounded wait that gives up ORs 2 into *status (may be null).
+// Returns cudaErrorCooperativeLaunchTooLarge when the grid cannot be resident at once.
+bool sweep_supported(int D, int mask, int code_bytes);
+bool sweep_fits(int H, int D, int code_bytes, int rows_per_cta);
+size_t sweep_scratch_bytes(int W, int H, int D, int rows_per_cta);
+cudaError_t launch_sweep(const void *codes, int code_bytes, int W, int H, int D, int nbits, int P1, int P2,
+                         int mask, int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
+                         void *scratch, unsigned *status, int rows_per_cta, cudaStream_t s);
+
 }  // namespace sgm

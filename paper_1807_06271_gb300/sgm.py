@@ -33,7 +33,12 @@ SGM_COST_KERNEL_AUTO = 0  # the faster one on GB300 (CUDA cores)
 SGM_COST_KERNEL_CUDA_CORES = 1  # POPC of the XOR of two codes, any D
 SGM_COST_KERNEL_TENSOR_CORES = 2  # +-1 inner products on tcgen05 (17 <= D <= 128)
 
-STAGES = ("census", "cost", "aggregate", "wta_lr", "median", "uvmap")
+STAGES = ("census", "cost", "aggregate", "wta_lr", "median", "uvmap", "sweep")
+
+# Path schedules (see sgm_set_schedule in include/sgm.h)
+SGM_SCHEDULE_AUTO = 0
+SGM_SCHEDULE_PLANES = 1  # independent scanlines over a cost volume, one plane per direction
+SGM_SCHEDULE_SWEEP = 2  # the paper's streaming set in one fused top-down sweep
 
 
 class SgmError(RuntimeError):
@@ -105,6 +110,8 @@ _SIGNATURES = {
     "sgm_debug_poke_canary": [_P, _I],
     "sgm_scratch_bytes": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P],
     "sgm_probe_int_rate": [_I, _I, _P, _P],
+    "sgm_set_schedule": [_P, _I, _I],
+    "sgm_get_schedule": [_P, _P, _P],
 }
 
 SGM_STATIC_SCRATCH_BYTES = 32 << 20
@@ -339,6 +346,18 @@ def sgm_debug_cost(h: Handle, left, right, C, kernel: int = SGM_COST_KERNEL_AUTO
     _check(load().sgm_debug_cost(
         h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"), kernel,
         _dev(C, ("uint16", "int16"), (h.H, h.W, h.D), "C"), _stream(stream)), "sgm_debug_cost")
+
+
+def sgm_set_schedule(h: Handle, schedule: int, rows_per_cta: int = 4):
+    """Path schedule of later calls on h (SGM_SCHEDULE_*)."""
+    _check(load().sgm_set_schedule(h.ptr, schedule, rows_per_cta), "sgm_set_schedule")
+
+
+def sgm_get_schedule(h: Handle):
+    """(schedule, rows_per_cta) in use on h."""
+    a, b = _I(), _I()
+    _check(load().sgm_get_schedule(h.ptr, ctypes.byref(a), ctypes.byref(b)), "sgm_get_schedule")
+    return a.value, b.value
 
 
 def sgm_set_cost_kernel(h: Handle, kernel: int):

@@ -180,6 +180,56 @@ int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
                       const uint8_t *const *right, uint8_t *const *disp,
                       uint16_t *const *umap, uint16_t *const *vmap, void *stream);
 
+/* ---- batch engine ----------------------------------------------------------
+ * Many pairs of uneven size and disparity range, each the method of Sec. 3.1
+ * with the same sgm_params, from one pooled device allocation.  A run is one
+ * CUDA graph: each pair's census and matching cost on a branch of its own,
+ * then per group of pairs one persistent aggregation launch whose work list
+ * holds every (pair, direction, scanline group) job of the group (the
+ * long-axis scanlines of all its pairs first), then each pair's WTA, right
+ * WTA and LR check, median and U/V maps on its branch.  Groups run side by
+ * side, so one group's WTA passes (bound by HBM) overlap another group's
+ * aggregation (bound by integer issue).  The paper has no counterpart. */
+typedef struct sgm_batch_s *sgm_batch;
+
+/* A batch of n pairs: pair i has W[i] x H[i] images and D[i] disparities.
+ * params are checked for every pair as by sgm_create; row_pitch must be 0
+ * (dense rows).  Allocates the pool (see sgm_batch_device_bytes) on the
+ * current device, one CUDA stream per pair, and starts with 1 group and 3
+ * resident aggregation blocks per SM. */
+int sgm_batch_create(int n, const int *W, const int *H, const int *D, const sgm_params *params,
+                     sgm_batch *out);
+
+/* Frees the batch (synchronises its device first). */
+int sgm_batch_destroy(sgm_batch b);
+
+/* Runs every pair: left[i]/right[i] device images (H[i] x W[i]), disp[i]
+ * device H[i] x W[i] output; umap/vmap NULL (no maps), or arrays of device
+ * D[i] x W[i] and H[i] x D[i] outputs (a NULL pair of entries skips that
+ * pair's maps).  The graph is captured on the first call and replayed while
+ * the same buffers and tuning come back.  Asynchronous on `stream`.  Calls on
+ * one batch must not overlap in time. */
+int sgm_batch_run(sgm_batch b, const uint8_t *const *left, const uint8_t *const *right,
+                  uint8_t *const *disp, uint16_t *const *umap, uint16_t *const *vmap, void *stream);
+
+/* Number of groups (a power of two up to 64, capped at the number of pairs;
+ * pairs are dealt to groups largest first) and the aggregation kernel's
+ * resident blocks per SM (1..16) of later runs.  Synchronises the device when
+ * the grouping changes. */
+int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm);
+int sgm_batch_get_tuning(sgm_batch b, int *groups, int *blocks_per_sm);
+
+/* Times runs on these buffers with 1, 2, 4, ... groups (up to one per pair)
+ * at 2, 3 and 4 blocks per SM and keeps the fastest; either output may be
+ * NULL.  Synchronises. */
+int sgm_batch_autotune(sgm_batch b, const uint8_t *const *left, const uint8_t *const *right,
+                       uint8_t *const *disp, uint16_t *const *umap, uint16_t *const *vmap,
+                       void *stream, int *best_groups, int *best_blocks_per_sm);
+
+/* Bytes of the batch's device pool: every pair's census codes, cost volume,
+ * path planes and LR map, plus the job tables and work-queue state. */
+int sgm_batch_device_bytes(sgm_batch b, size_t *bytes);
+
 /* Path schedules: how the aggregation of Eq. 2 is organised on the GPU.
  *   PLANES: every enabled direction is cut into independent scanlines that
  *     run concurrently over a materialised cost volume and write one plane

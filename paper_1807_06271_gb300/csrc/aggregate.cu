@@ -288,21 +288,20 @@ __device__ __forceinline__ typename Lane<DPL, WIDE>::T pack_plane(const PathStat
     return chunk_of<CT>(w);
 }
 
+// One job: the G neighbouring scanlines s0 .. s0+G-1 of one direction
+// (dx, dy), scanline s0 + grp for this lane's group, written to plane
+// `plane` of `nplanes`.
 template <int LPS, int DPL, bool WIDE, bool RAGGED, int PF>
-__global__ void __launch_bounds__(kWarps * 32)
-    aggregate_kernel(const typename Lane<DPL, WIDE>::T *__restrict__ cost, int W, int H, int D,
-                     uint32_t P1x2, uint32_t P2x2, PathJobs jobs,
-                     typename Lane<DPL, WIDE>::T *__restrict__ planes, int nplanes,
-                     unsigned *__restrict__ job_counter) {
-    wait_for_predecessor();
+__device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__restrict__ cost,
+                                        typename Lane<DPL, WIDE>::T *__restrict__ planes, int W, int H, int D,
+                                        int nplanes, int dx, int dy, int plane, int nlines, int s0,
+                                        uint32_t P1x2, uint32_t P2x2, uint64_t pol_stream) {
     using CT = typename Lane<DPL, WIDE>::T;
-    constexpr int G = 32 / LPS, NR = DPL / 2;
+    constexpr int NR = DPL / 2;
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPS, li = lane % LPS;
     const uint32_t lo_edge = li == 0 ? 0x7FFFu : 0u;            // no d = -1
     const uint32_t hi_edge = li == LPS - 1 ? 0x7FFF0000u : 0u;  // no d = Dp
-    const int total = jobs.jbegin[jobs.n];
-    const uint64_t pol_stream = policy_evict_first();
     uint32_t inv[NR];
 #pragma unroll
     for (int k = 0; k < NR; k++) {
@@ -310,6 +309,99 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (RAGGED)
             inv[k] = (DPL * li + k >= D ? 0x7FFFu : 0u) | (DPL * li + k + NR >= D ? 0x7FFF0000u : 0u);
     }
+    const int s = s0 + grp;
+    int x = 0, y = 0, len = 0;
+    if (s < nlines) {
+        if (dy == 0) {
+            y = s;
+            x = dx > 0 ? 0 : W - 1;
+            len = W;
+        } else if (dx == 0) {
+            x = s;
+            y = dy > 0 ? 0 : H - 1;
+            len = H;
+        } else if (s < W) {
+            x = s;
+            y = dy > 0 ? 0 : H - 1;
+            len = min(dx > 0 ? W - s : s + 1, H);
+        } else {
+            const int tt = s - W + 1;
+            x = dx > 0 ? 0 : W - 1;
+            y = dy > 0 ? tt : H - 1 - tt;
+            len = min(H - tt, W);
+        }
+    }
+    const int steps = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+    // chunk indices: cost chunk (x, y, li) is cost[(y*W + x)*LPS + li], plane
+    // chunk is planes[((y*W + x)*nplanes + plane)*LPS + li] (all planes of a
+    // pixel are adjacent).  Indices stay below 2^31 (checked at handle creation).
+    const int pix = y * W + x;
+    const int cstep = (dy * W + dx) * LPS;
+    const int ostep = cstep * nplanes;
+    int ci_ld = pix * LPS + li;  // next cost chunk to load into the ring
+    int oi = (pix * nplanes + plane) * LPS + li;
+    CT ring[PF];
+#pragma unroll
+    for (int i = 0; i < PF; i++) {
+        ring[i] = i < len ? ld_chunk(cost + ci_ld) : zero_chunk<CT>();
+        ci_ld += cstep;
+    }
+    PathState<DPL> st;
+#pragma unroll
+    for (int q = 0; q < NR; q++) st.R[q] = inv[q];
+    st.m2 = 0u;
+    st.mP2 = P2x2;
+    int rem = len;  // steps of this lane's scanline not yet taken
+    int t0 = 0;
+    // While every scanline of the warp has at least 2 * PF steps left, the
+    // loads and stores need no checks.
+    const int minlen = (int)__reduce_min_sync(0xffffffffu, (unsigned)len);
+    for (; t0 + 2 * PF <= minlen; t0 += PF) {
+#pragma unroll
+        for (int i = 0; i < PF; i++) {
+            const CT c = ring[i];
+            ring[i] = ld_chunk(cost + ci_ld);
+            ci_ld += cstep;
+            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+            st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
+            oi += ostep;
+        }
+        rem -= PF;
+    }
+    for (; t0 + PF <= steps; t0 += PF) {
+#pragma unroll
+        for (int i = 0; i < PF; i++) {
+            const CT c = ring[i];
+            if (rem > PF) ring[i] = ld_chunk(cost + ci_ld);
+            ci_ld += cstep;
+            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+            if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
+            oi += ostep;
+            rem--;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PF; i++) {  // the last steps < PF
+        if (t0 + i < steps) {
+            path_step<LPS, DPL, WIDE, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+            if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
+            oi += ostep;
+            rem--;
+        }
+    }
+}
+
+template <int LPS, int DPL, bool WIDE, bool RAGGED, int PF>
+__global__ void __launch_bounds__(kWarps * 32)
+    aggregate_kernel(const typename Lane<DPL, WIDE>::T *__restrict__ cost, int W, int H, int D,
+                     uint32_t P1x2, uint32_t P2x2, PathJobs jobs,
+                     typename Lane<DPL, WIDE>::T *__restrict__ planes, int nplanes,
+                     unsigned *__restrict__ job_counter) {
+    wait_for_predecessor();
+    constexpr int G = 32 / LPS;
+    const int lane = threadIdx.x & 31;
+    const int total = jobs.jbegin[jobs.n];
+    const uint64_t pol_stream = policy_evict_first();
     bool first = true;
     for (;;) {
         unsigned job = 0;
@@ -319,87 +411,69 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (job >= (unsigned)total) return;
         int k = 0;
         while ((int)job >= jobs.jbegin[k + 1]) k++;
-        const int s = ((int)job - jobs.jbegin[k]) * G + grp;
-        const int dx = jobs.dx[k], dy = jobs.dy[k];
-        int x = 0, y = 0, len = 0;
-        if (s < jobs.nlines[k]) {
-            if (dy == 0) {
-                y = s;
-                x = dx > 0 ? 0 : W - 1;
-                len = W;
-            } else if (dx == 0) {
-                x = s;
-                y = dy > 0 ? 0 : H - 1;
-                len = H;
-            } else if (s < W) {
-                x = s;
-                y = dy > 0 ? 0 : H - 1;
-                len = min(dx > 0 ? W - s : s + 1, H);
-            } else {
-                const int tt = s - W + 1;
-                x = dx > 0 ? 0 : W - 1;
-                y = dy > 0 ? tt : H - 1 - tt;
-                len = min(H - tt, W);
-            }
+        run_job<LPS, DPL, WIDE, RAGGED, PF>(cost, planes, W, H, D, nplanes, jobs.dx[k], jobs.dy[k], jobs.plane[k],
+                                            jobs.nlines[k], ((int)job - jobs.jbegin[k]) * G, P1x2, P2x2, pol_stream);
+    }
+}
+
+// Many pairs in one persistent launch.  The work list of pair p is its
+// PathJobs; the two queues number all pairs' long-axis jobs (queue 0) and
+// all their other jobs (queue 1) in pair order, pair p's starting at
+// pfx[0][p] and pfx[1][p].  Each job runs with its pair's lanes per scanline.
+template <int DPL, bool WIDE, int PF>
+__global__ void __launch_bounds__(kWarps * 32)
+    aggregate_batch_kernel(const BatchAggPair *__restrict__ pairs, int npairs, const int *__restrict__ prefix,
+                           uint32_t P1x2, uint32_t P2x2, unsigned *__restrict__ job_counter) {
+    wait_for_predecessor();
+    extern __shared__ int spfx[];  // [2][npairs + 1]
+    for (int i = threadIdx.x; i < 2 * (npairs + 1); i += blockDim.x) spfx[i] = prefix[i];
+    __syncthreads();
+    using CT = typename Lane<DPL, WIDE>::T;
+    const int lane = threadIdx.x & 31;
+    const int nlong = spfx[npairs], nother = spfx[npairs + 1 + npairs];
+    const int total = nlong + nother;
+    const uint64_t pol_stream = policy_evict_first();
+    bool first = true;
+    for (;;) {
+        unsigned job = 0;
+        if (lane == 0) job = next_job(job_counter, (unsigned)nlong, (unsigned)total, first);
+        first = false;
+        job = __shfl_sync(0xffffffffu, job, 0);
+        if (job >= (unsigned)total) return;
+        // the pair: binary search in the queue's prefix
+        const bool lq = (int)job < nlong;
+        const int *q = lq ? spfx : spfx + npairs + 1;
+        const int jq = lq ? (int)job : (int)job - nlong;
+        int lo = 0, hi = npairs;  // q[lo] <= jq < q[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (q[mid] <= jq) lo = mid;
+            else hi = mid;
         }
-        const int steps = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
-        // chunk indices: cost chunk (x, y, li) is cost[(y*W + x)*LPS + li], plane
-        // chunk is planes[((y*W + x)*nplanes + plane)*LPS + li] (all planes of a
-        // pixel are adjacent).  Indices stay below 2^31 (checked at handle creation).
-        const int pix = y * W + x;
-        const int cstep = (dy * W + dx) * LPS;
-        const int ostep = cstep * nplanes;
-        int ci_ld = pix * LPS + li;  // next cost chunk to load into the ring
-        int oi = (pix * nplanes + jobs.plane[k]) * LPS + li;
-        CT ring[PF];
-#pragma unroll
-        for (int i = 0; i < PF; i++) {
-            ring[i] = i < len ? ld_chunk(cost + ci_ld) : zero_chunk<CT>();
-            ci_ld += cstep;
+        const BatchAggPair &p = pairs[lo];
+        const int local = lq ? jq - q[lo] : p.jobs.nlong + (jq - q[lo]);
+        int k = 0;
+        while (local >= p.jobs.jbegin[k + 1]) k++;
+        const int G = 32 / p.lps;
+        const int s0 = (local - p.jobs.jbegin[k]) * G;
+        const CT *cost = reinterpret_cast<const CT *>(p.cost);
+        CT *planes = reinterpret_cast<CT *>(p.planes);
+#define SGM_JOB(L, RG)                                                                                      \
+    run_job<L, DPL, WIDE, RG, PF>(cost, planes, p.W, p.H, p.D, p.nplanes, p.jobs.dx[k], p.jobs.dy[k],       \
+                                  p.jobs.plane[k], p.jobs.nlines[k], s0, P1x2, P2x2, pol_stream)
+#define SGM_JOB_L(L)              \
+    if (p.ragged) SGM_JOB(L, true); \
+    else SGM_JOB(L, false)
+        switch (p.lps) {
+            case 1: SGM_JOB_L(1); break;
+            case 2: SGM_JOB_L(2); break;
+            case 4: SGM_JOB_L(4); break;
+            case 8: SGM_JOB_L(8); break;
+            case 16: SGM_JOB_L(16); break;
+            default: SGM_JOB_L(32); break;
         }
-        PathState<DPL> st;
-#pragma unroll
-        for (int q = 0; q < NR; q++) st.R[q] = inv[q];
-        st.m2 = 0u;
-        st.mP2 = P2x2;
-        int rem = len;  // steps of this lane's scanline not yet taken
-        int t0 = 0;
-        // While every scanline of the warp has at least 2 * PF steps left, the
-        // loads and stores need no checks.
-        const int minlen = (int)__reduce_min_sync(0xffffffffu, (unsigned)len);
-        for (; t0 + 2 * PF <= minlen; t0 += PF) {
-#pragma unroll
-            for (int i = 0; i < PF; i++) {
-                const CT c = ring[i];
-                ring[i] = ld_chunk(cost + ci_ld);
-                ci_ld += cstep;
-                path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
-                oi += ostep;
-            }
-            rem -= PF;
-        }
-        for (; t0 + PF <= steps; t0 += PF) {
-#pragma unroll
-            for (int i = 0; i < PF; i++) {
-                const CT c = ring[i];
-                if (rem > PF) ring[i] = ld_chunk(cost + ci_ld);
-                ci_ld += cstep;
-                path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
-                oi += ostep;
-                rem--;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PF; i++) {  // the last steps < PF
-            if (t0 + i < steps) {
-                path_step<LPS, DPL, WIDE, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
-                if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
-                oi += ostep;
-                rem--;
-            }
-        }
+#undef SGM_JOB_L
+#undef SGM_JOB
     }
 }
 
@@ -466,6 +540,23 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
     const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
     if (wide) return launch_all<true>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
     return launch_all<false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+}
+
+cudaError_t launch_aggregate_batch(const BatchAggPair *pairs, int npairs, const int *prefix, int P1, int P2,
+                                   bool wide, unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
+    if (npairs <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * (blocks_per_sm > 0 ? blocks_per_sm : 2);
+    const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
+    const size_t smem = sizeof(int) * 2 * (size_t)(npairs + 1);
+    if (wide)
+        return launch_k(aggregate_batch_kernel<8, true, 8>, dim3(blocks), dim3(kWarps * 32), smem, s, pairs, npairs,
+                        prefix, P1x2, P2x2, job_counter);
+    return launch_k(aggregate_batch_kernel<8, false, 16>, dim3(blocks), dim3(kWarps * 32), smem, s, pairs, npairs,
+                    prefix, P1x2, P2x2, job_counter);
 }
 
 cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,

@@ -120,6 +120,17 @@ constexpr size_t kJobStateBytes = (size_t)(kJobClaimBase + kJobClaimSlots) * siz
 // increasing direction order), longest scanlines first; G = 32 / LPS.
 PathJobs make_path_jobs(int W, int H, int D, int mask);
 
+// One pair of a batched aggregation launch (device-resident table entry).
+struct BatchAggPair {
+    const void *cost;  // the pair's cost volume
+    void *planes;      // its path planes
+    int W, H, D;
+    int lps;           // lanes per scanline for D
+    int ragged;        // D < 8 * lps
+    int nplanes;
+    PathJobs jobs;
+};
+
 }  // namespace sgm
 
 namespace sgm {
@@ -155,6 +166,12 @@ cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch
 cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2, bool wide,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
                              unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
+// All pairs' aggregation in one persistent launch (pairs: device table of
+// npairs entries; prefix: device [2][npairs + 1], the running counts of the
+// pairs' long-axis jobs and of their other jobs).  job_counter as above, for
+// this launch alone.  P1/P2 and the cost width are shared by the pairs.
+cudaError_t launch_aggregate_batch(const BatchAggPair *pairs, int npairs, const int *prefix, int P1, int P2,
+                                   bool wide, unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
 // Copies a single plane ([H][W][Dp], lane-chunk order) to L ([H][W][D] uint16, natural order).
 cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,
                              cudaStream_t s);

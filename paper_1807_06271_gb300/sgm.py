@@ -111,6 +111,13 @@ _SIGNATURES = {
     "sgm_scratch_bytes": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P],
     "sgm_probe_int_rate": [_I, _I, _P, _P],
     "sgm_set_schedule": [_P, _I, _I],
+    "sgm_batch_create": [_I, _P, _P, _P, ctypes.POINTER(_Params), ctypes.POINTER(_P)],
+    "sgm_batch_destroy": [_P],
+    "sgm_batch_run": [_P, _P, _P, _P, _P, _P, _P],
+    "sgm_batch_set_tuning": [_P, _I, _I],
+    "sgm_batch_get_tuning": [_P, _P, _P],
+    "sgm_batch_autotune": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "sgm_batch_device_bytes": [_P, _P],
     "sgm_get_schedule": [_P, _P, _P],
 }
 
@@ -346,6 +353,108 @@ def sgm_debug_cost(h: Handle, left, right, C, kernel: int = SGM_COST_KERNEL_AUTO
     _check(load().sgm_debug_cost(
         h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"), kernel,
         _dev(C, ("uint16", "int16"), (h.H, h.W, h.D), "C"), _stream(stream)), "sgm_debug_cost")
+
+
+class Batch:
+    """Owns one sgm_batch: n pairs of sizes shapes[i] = (W, H, D), one set of
+    parameters, one pooled device allocation (see sgm_batch_* in sgm.h)."""
+
+    def __init__(self, shapes, params: SgmParams | None = None):
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.params = params or SgmParams()
+        n = len(self.shapes)
+        Ws = (ctypes.c_int * n)(*[sh[0] for sh in self.shapes])
+        Hs = (ctypes.c_int * n)(*[sh[1] for sh in self.shapes])
+        Ds = (ctypes.c_int * n)(*[sh[2] for sh in self.shapes])
+        p = self.params._c()
+        out = _P()
+        _check(load().sgm_batch_create(n, Ws, Hs, Ds, ctypes.byref(p), ctypes.byref(out)), "sgm_batch_create")
+        self._b = out.value
+
+    @property
+    def ptr(self):
+        return self._b
+
+    def close(self):
+        if self._b:
+            load().sgm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _arrays(self, left, right, disp, umap, vmap):
+        n = len(self.shapes)
+        if not (len(left) == len(right) == len(disp) == n):
+            raise ValueError("one left, right and disp tensor per pair")
+        L = (_P * n)(*[_dev(t, ("uint8",), (H, W), "left") for t, (W, H, D) in zip(left, self.shapes)])
+        R = (_P * n)(*[_dev(t, ("uint8",), (H, W), "right") for t, (W, H, D) in zip(right, self.shapes)])
+        O = (_P * n)(*[_dev(t, ("uint8",), (H, W), "disp") for t, (W, H, D) in zip(disp, self.shapes)])
+        if umap is None:
+            return L, R, O, None, None
+        U = (_P * n)(*[_dev(t, ("uint16", "int16"), (D, W), "umap") for t, (W, H, D) in zip(umap, self.shapes)])
+        V = (_P * n)(*[_dev(t, ("uint16", "int16"), (H, D), "vmap") for t, (W, H, D) in zip(vmap, self.shapes)])
+        return L, R, O, U, V
+
+    def run(self, left, right, disp, umap=None, vmap=None, stream=None):
+        _check(load().sgm_batch_run(self._b, *self._arrays(left, right, disp, umap, vmap), _stream(stream)),
+               "sgm_batch_run")
+
+    def set_tuning(self, groups: int, blocks_per_sm: int):
+        _check(load().sgm_batch_set_tuning(self._b, groups, blocks_per_sm), "sgm_batch_set_tuning")
+
+    def tuning(self):
+        g, b = _I(), _I()
+        _check(load().sgm_batch_get_tuning(self._b, ctypes.byref(g), ctypes.byref(b)), "sgm_batch_get_tuning")
+        return g.value, b.value
+
+    def autotune(self, left, right, disp, umap=None, vmap=None, stream=None):
+        g, b = _I(), _I()
+        _check(load().sgm_batch_autotune(self._b, *self._arrays(left, right, disp, umap, vmap), _stream(stream),
+                                         ctypes.byref(g), ctypes.byref(b)), "sgm_batch_autotune")
+        return g.value, b.value
+
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(load().sgm_batch_device_bytes(self._b, ctypes.byref(v)), "sgm_batch_device_bytes")
+        return v.value
+
+
+def sgm_batch_create(shapes, params: SgmParams | None = None) -> Batch:
+    return Batch(shapes, params)
+
+
+def sgm_batch_destroy(b: Batch):
+    b.close()
+
+
+def sgm_batch_run(b: Batch, left, right, disp, umap=None, vmap=None, stream=None):
+    b.run(left, right, disp, umap, vmap, stream)
+
+
+def sgm_batch_set_tuning(b: Batch, groups: int, blocks_per_sm: int):
+    b.set_tuning(groups, blocks_per_sm)
+
+
+def sgm_batch_get_tuning(b: Batch):
+    return b.tuning()
+
+
+def sgm_batch_autotune(b: Batch, left, right, disp, umap=None, vmap=None, stream=None):
+    return b.autotune(left, right, disp, umap, vmap, stream)
+
+
+def sgm_batch_device_bytes(b: Batch) -> int:
+    return b.device_bytes()
 
 
 def sgm_set_schedule(h: Handle, schedule: int, rows_per_cta: int = 4):

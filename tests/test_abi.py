@@ -248,3 +248,24 @@ def test_static_limit_follows_the_scratch_query():
     big = sgm.SgmParams(census_w=9, census_h=7, path_mask=sgm.SGM_PATHS_8, P1=8, P2=96)
     assert sgm.sgm_scratch_bytes(320, 240, 64, small)[2] <= sgm.SGM_STATIC_SCRATCH_BYTES
     assert sgm.sgm_scratch_bytes(1242, 375, 128, big)[2] > sgm.SGM_STATIC_SCRATCH_BYTES
+
+
+def test_batch_entry_points_check_their_arguments_on_the_host():
+    """Null batch or null arrays: SGM_ERR_INVALID_ARG; bad shapes or
+    parameters are refused before anything is allocated (no GPU needed)."""
+    lib = sgm.load()
+    for name in ("sgm_batch_destroy", "sgm_batch_run", "sgm_batch_set_tuning", "sgm_batch_get_tuning",
+                 "sgm_batch_autotune", "sgm_batch_device_bytes"):
+        fn = getattr(lib, name)
+        args = [0 if t is ctypes.c_int else None for t in fn.argtypes]
+        assert fn(*args) == sgm.SGM_ERR_INVALID_ARG, name
+    p = sgm.SgmParams(census_w=9, census_h=7, path_mask=0xFF, P1=8, P2=96)._c()
+    out = ctypes.c_void_p()
+    W, H, D = (ctypes.c_int * 2)(64, 32), (ctypes.c_int * 2)(48, 16), (ctypes.c_int * 2)(64, 300)
+    assert lib.sgm_batch_create(2, W, H, D, ctypes.byref(p), ctypes.byref(out)) == sgm.SGM_ERR_UNSUPPORTED
+    assert lib.sgm_batch_create(0, W, H, D, ctypes.byref(p), ctypes.byref(out)) == sgm.SGM_ERR_INVALID_ARG
+    assert lib.sgm_batch_create(2, W, H, None, ctypes.byref(p), ctypes.byref(out)) == sgm.SGM_ERR_INVALID_ARG
+    pitched = sgm.SgmParams(row_pitch=128)._c()
+    D2 = (ctypes.c_int * 2)(64, 64)
+    assert lib.sgm_batch_create(2, W, H, D2, ctypes.byref(pitched), ctypes.byref(out)) == sgm.SGM_ERR_INVALID_ARG
+    assert out.value is None

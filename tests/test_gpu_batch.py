@@ -139,3 +139,110 @@ def test_64_pair_mixed_batch_equals_single_pair_launches():
         o = oracle.sgm(s.left, s.right, D, 9, 7, sgm.SGM_PATHS_8, 8, 96, 1, 3)
         assert np.array_equal(b.Dd[i].cpu().numpy(), o["disp"]), i
     b.close()
+
+
+# ---- the batch engine (sgm_batch_*): pooled scratch, one persistent
+# aggregation launch per group over all its pairs' jobs ----------------------
+
+class Engine:
+    """The same pairs through sgm_batch_*; reference maps from single handles."""
+
+    def __init__(self, specs, params=P8, seed0=300):
+        self.specs, self.params = specs, sgm.SgmParams(**params)
+        self.scenes = [make_pair(W, H, D, seed0 + i) for i, (W, H, D) in enumerate(specs)]
+        self.L = [torch.from_numpy(s.left).cuda() for s in self.scenes]
+        self.R = [torch.from_numpy(s.right).cuda() for s in self.scenes]
+        self.Dd = [torch.full((H, W), 7, dtype=torch.uint8, device="cuda") for W, H, D in specs]
+        self.U = [torch.empty((D, W), dtype=torch.int16, device="cuda") for W, H, D in specs]
+        self.V = [torch.empty((H, D), dtype=torch.int16, device="cuda") for W, H, D in specs]
+        self.b = sgm.Batch(specs, self.params)
+
+    def run(self, maps=True):
+        self.b.run(self.L, self.R, self.Dd, self.U if maps else None, self.V if maps else None)
+        torch.cuda.synchronize()
+
+    def single(self, i):
+        W, H, D = self.specs[i]
+        with sgm.Handle(W, H, D, self.params) as h:
+            d = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+            u = torch.empty((D, W), dtype=torch.int16, device="cuda")
+            v = torch.empty((H, D), dtype=torch.int16, device="cuda")
+            h.compute(self.L[i], self.R[i], d)
+            h.uvmap(d, u, v)
+            torch.cuda.synchronize()
+            return d.cpu().numpy(), u16(u), u16(v)
+
+    def check_all(self, maps=True):
+        for i in range(len(self.specs)):
+            d, u, v = self.single(i)
+            assert np.array_equal(self.Dd[i].cpu().numpy(), d), f"pair {i} {self.specs[i]}"
+            if maps:
+                assert np.array_equal(u16(self.U[i]), u) and np.array_equal(u16(self.V[i]), v), i
+
+
+@pytest.mark.parametrize("groups,bps", [(1, 3), (2, 2), (4, 4), (8, 1)])
+def test_engine_matches_single_pairs_at_each_tuning(groups, bps):
+    specs = [(160, 96, 64), (97, 61, 128), (64, 40, 32), (300, 20, 16), (20, 200, 48), (257, 33, 128),
+             (45, 45, 100), (128, 64, 255), (1, 9, 8)]
+    e = Engine(specs, seed0=500 + groups)
+    e.b.set_tuning(groups, bps)
+    assert e.b.tuning() == (min(groups, len(specs)), bps)
+    e.run()
+    e.check_all()
+    for i in (0, 2, 6):  # and the oracle, on a few
+        W, H, D = specs[i]
+        s = e.scenes[i]
+        o = oracle.sgm(s.left, s.right, D, 9, 7, sgm.SGM_PATHS_8, 8, 96, 1, 3)
+        assert np.array_equal(e.Dd[i].cpu().numpy(), o["disp"]), i
+        assert np.array_equal(u16(e.U[i]), o["U"]) and np.array_equal(u16(e.V[i]), o["V"]), i
+    e.b.close()
+
+
+def test_engine_replays_with_new_contents_and_without_maps():
+    specs = [(120, 80, 64), (80, 50, 16), (150, 40, 128)]
+    e = Engine(specs, seed0=70)
+    e.run()
+    for i, (W, H, D) in enumerate(specs):  # new contents, same buffers: the replay reads them
+        s = make_pair(W, H, D, 970 + i)
+        e.L[i].copy_(torch.from_numpy(s.left))
+        e.R[i].copy_(torch.from_numpy(s.right))
+    e.run()
+    e.check_all()
+    e.run(maps=False)  # a second graph, without the maps
+    e.check_all(maps=False)
+    e.b.close()
+
+
+def test_engine_other_parameter_sets():
+    """4-path 5x5 census with no median, and the SAD cost with the paper's
+    penalties on the streaming set: each pair equal to its single launch."""
+    specs = [(130, 70, 64), (90, 40, 60), (200, 30, 128)]
+    for params in (dict(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_4, P1=4, P2=24, lr_tolerance=0, median_k=0),
+                   dict(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_STREAM4, P1=200, P2=800, lr_tolerance=1,
+                        median_k=5, cost=sgm.SGM_COST_SAD)):
+        e = Engine(specs, params=params, seed0=20)
+        e.run()
+        e.check_all()
+        e.b.close()
+
+
+def test_engine_64_mixed_pairs_autotuned():
+    """The batched workload through the engine: 64 pairs of sizes from
+    {320x240, 640x480, 1242x375, 1280x720} and D from {64, 128}; autotuned,
+    then every pair byte-identical to its single launch; the pool's size is
+    reported."""
+    rng = scenes.Rng(1807 + 3)
+    sizes = [(320, 240), (640, 480), (1242, 375), (1280, 720)]
+    si = rng.integers(0, 3, 64)
+    di = rng.integers(0, 1, 64)
+    specs = [(sizes[a][0], sizes[a][1], (64, 128)[b]) for a, b in zip(si, di)]
+    e = Engine(specs, seed0=1807 + 3)
+    g, bps = e.b.autotune(e.L, e.R, e.Dd, e.U, e.V)
+    assert g in (1, 2, 4, 8, 16, 32, 64) and bps in (2, 3, 4)
+    e.run()
+    e.check_all()
+    # each handle would also hold its own work-queue state (4228 bytes); the
+    # engine keeps one per group
+    per_pair = sum(sgm.sgm_scratch_bytes(W, H, D, e.params)[0] - 4228 for W, H, D in specs)
+    assert per_pair <= e.b.device_bytes() < per_pair + (1 << 20)
+    e.b.close()

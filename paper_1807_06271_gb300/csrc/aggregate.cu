@@ -21,10 +21,12 @@
 // themselves, and those of the first and last cost one byte-permute each
 // with the value fetched from the neighbouring lane (one shuffle each way).
 // One update is
-//     t = min(min(L(d-1), L(d+1)) + P1, L(d), m + P2);   L' = t + C - m
-// evaluated two disparities at a time with the full-rate min.u16x2 and plain
-// 32-bit adds (no half ever carries: values stay below 0x7FFF + 255, and
-// t >= m makes t + C - m non-negative in each half).  m = min_d L is reduced
+//     t = min(min(L(d-1), L(d+1), m + P2 - P1) + P1, L(d));   L' = t + C - m
+// (the same minimum as min(L(d±1) + P1, L(d), m + P2)), evaluated two
+// disparities at a time with a three-way packed minimum, a packed
+// add-then-minimum and a plain 32-bit three-input add (no half ever carries:
+// values stay below 0x7FFF + 255, and t >= m makes t + C - m non-negative in
+// each half).  m = min_d L is reduced
 // within the lane (min.u16x2), then across the scanline's lanes: xor-shuffles
 // for scanlines of up to 4 lanes, one full-warp redux.sync per scanline of
 // the warp for wider ones (an xor-shuffle tree over 16 lanes measured 1.5x
@@ -214,17 +216,17 @@ __device__ __forceinline__ uint32_t line_min2(uint32_t x, int grp) {
 }
 
 // Path state of one lane: R[k] = (L[k], L[k+h]) packed (h = DPL/2),
-// m2 = (m, m), mP2 = m2 + (P2, P2).
+// m2 = (m, m), mQ = m2 + (P2 - P1, P2 - P1).
 template <int DPL>
 struct PathState {
     uint32_t R[DPL / 2];
-    uint32_t m2, mP2;
+    uint32_t m2, mQ;
 };
 
 // One step of Eq. 2 for the lane's DPL disparities with cost chunk c.
 template <int LPS, int DPL, bool WIDE, bool RAGGED>
 __device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Lane<DPL, WIDE>::T &c,
-                                          uint32_t P1x2, uint32_t P2x2, int grp, uint32_t lo_edge,
+                                          uint32_t P1x2, uint32_t QPx2, int grp, uint32_t lo_edge,
                                           uint32_t hi_edge, const uint32_t (&inv)[DPL / 2]) {
     constexpr int NR = DPL / 2;
     uint32_t cc[NR];
@@ -250,7 +252,11 @@ __device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Lan
     for (int k = 0; k < NR; k++) {
         const uint32_t lm = k == 0 ? dm0 : st.R[k - 1];
         const uint32_t rm = k == NR - 1 ? dpN : st.R[k + 1];
-        n[k] = vmin2(vmin2(vmin2(lm, rm) + P1x2, st.R[k]), st.mP2) + cc[k] - st.m2;
+        // min(L(d-1) + P1, L(d+1) + P1, m + P2, L(d)) as min(min(L(d-1), L(d+1),
+        // m + P2 - P1) + P1, L(d)): a three-way packed minimum and a packed
+        // add-then-minimum (the dynamic-programming instructions of sm_90+);
+        // no half wraps, as every value stays below 0x7FFF + P1
+        n[k] = __viaddmin_u16x2(__vimin3_u16x2(lm, rm, st.mQ), P1x2, st.R[k]) + cc[k] - st.m2;
         if (RAGGED) n[k] = vmax2(n[k], inv[k]);
     }
     uint32_t mn = n[0];
@@ -260,7 +266,7 @@ __device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Lan
         if (k) mn = vmin2(mn, n[k]);
     }
     st.m2 = line_min2<LPS>(mn, grp);
-    st.mP2 = st.m2 + P2x2;
+    st.mQ = st.m2 + QPx2;
 }
 
 // The lane's DPL path costs in the cost volume's order.  Padding slots
@@ -350,7 +356,7 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
 #pragma unroll
     for (int q = 0; q < NR; q++) st.R[q] = inv[q];
     st.m2 = 0u;
-    st.mP2 = P2x2;
+    st.mQ = P2x2 - P1x2;
     int rem = len;  // steps of this lane's scanline not yet taken
     int t0 = 0;
     // While every scanline of the warp has at least 2 * PF steps left, the
@@ -362,7 +368,7 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
             const CT c = ring[i];
             ring[i] = ld_chunk(cost + ci_ld);
             ci_ld += cstep;
-            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2 - P1x2, grp, lo_edge, hi_edge, inv);
             st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
             oi += ostep;
         }
@@ -374,7 +380,7 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
             const CT c = ring[i];
             if (rem > PF) ring[i] = ld_chunk(cost + ci_ld);
             ci_ld += cstep;
-            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2 - P1x2, grp, lo_edge, hi_edge, inv);
             if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
             oi += ostep;
             rem--;
@@ -383,7 +389,7 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
 #pragma unroll
     for (int i = 0; i < PF; i++) {  // the last steps < PF
         if (t0 + i < steps) {
-            path_step<LPS, DPL, WIDE, RAGGED>(st, ring[i], P1x2, P2x2, grp, lo_edge, hi_edge, inv);
+            path_step<LPS, DPL, WIDE, RAGGED>(st, ring[i], P1x2, P2x2 - P1x2, grp, lo_edge, hi_edge, inv);
             if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
             oi += ostep;
             rem--;

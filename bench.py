@@ -797,7 +797,8 @@ def batch_summary(torch, sgm, steps, warmup):
     bs = BatchSet(torch, sgm)
     batch_ms, graph_ms, seq_ms, tuning = batch_timings(torch, sgm, bs, steps, warmup)
     out = {"config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(bs.specs), "de_per_step": bs.de,
-                      "engine_groups": tuning[0], "engine_blocks_per_sm": tuning[1]},
+                      "engine_groups": tuning[0], "engine_blocks_per_sm": tuning[1],
+                      "engine_chunks_per_lane": tuning[2]},
            "value": bs.de / (batch_ms / 1e3) / 1e6, "unit": "MDE/s", "ms_per_step": batch_ms, "steps": steps,
            "api": "sgm_batch_run (pooled scratch, one aggregation launch per group)",
            "graph_of_handles": {"ms_per_step": graph_ms, "value": bs.de / (graph_ms / 1e3) / 1e6,
@@ -825,6 +826,7 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": "batch-64-mixed-census9x7-8path", "pairs": len(bs.specs),
                        "de_per_step": bs.de, "engine_groups": tuning[0], "engine_blocks_per_sm": tuning[1],
+                       "engine_chunks_per_lane": tuning[2],
                        "tuned_blocks_per_sm": {f"{k[0]}x{k[1]}d{k[2]}": v for k, v in bs.tuned.items()}},
             "graph_of_handles": {"ms_per_step": graph_ms, "value": bs.de / (graph_ms / 1e3) / 1e6},
             "one_pair_per_launch": {"ms_per_step": seq_ms, "value": bs.de / (seq_ms / 1e3) / 1e6},

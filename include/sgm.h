@@ -213,22 +213,36 @@ int sgm_batch_run(sgm_batch b, const uint8_t *const *left, const uint8_t *const 
                   uint8_t *const *disp, uint16_t *const *umap, uint16_t *const *vmap, void *stream);
 
 /* Number of groups (a power of two up to 64, capped at the number of pairs;
- * pairs are dealt to groups largest first) and the aggregation kernel's
- * resident blocks per SM (1..16) of later runs.  Synchronises the device when
- * the grouping changes. */
-int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm);
-int sgm_batch_get_tuning(sgm_batch b, int *groups, int *blocks_per_sm);
+ * pairs are dealt to groups largest first), the aggregation kernel's
+ * resident blocks per SM (1..16) and its 8-disparity chunks per lane (1, or
+ * 4 when every pair's D spans at least 4 chunks and the cost is census; see
+ * sgm_set_aggregation) of later runs.  Synchronises the device when the
+ * grouping or the chunks per lane change. */
+int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm, int chunks_per_lane);
+int sgm_batch_get_tuning(sgm_batch b, int *groups, int *blocks_per_sm, int *chunks_per_lane);
 
 /* Times runs on these buffers with 1, 2, 4, ... groups (up to one per pair)
- * at 2, 3 and 4 blocks per SM and keeps the fastest; either output may be
- * NULL.  Synchronises. */
+ * at 2, 3 and 4 blocks per SM, each with 1 and (where allowed) 4 chunks per
+ * lane, and keeps the fastest; any output may be NULL.  Synchronises. */
 int sgm_batch_autotune(sgm_batch b, const uint8_t *const *left, const uint8_t *const *right,
                        uint8_t *const *disp, uint16_t *const *umap, uint16_t *const *vmap,
-                       void *stream, int *best_groups, int *best_blocks_per_sm);
+                       void *stream, int *best_groups, int *best_blocks_per_sm, int *best_chunks_per_lane);
 
 /* Bytes of the batch's device pool: every pair's census codes, cost volume,
  * path planes and LR map, plus the job tables and work-queue state. */
 int sgm_batch_device_bytes(sgm_batch b, size_t *bytes);
+
+/* Shape of the aggregation kernel of later calls on h (the paper has no
+ * counterpart): resident 4-warp blocks per SM (1..16) and 8-disparity chunks
+ * per lane (1, 2 or 4; SGM_ERR_UNSUPPORTED above what D allows: D must span
+ * at least that many chunks, and the 16-bit costs of SGM_COST_SAD take 1).
+ * With c chunks per lane a scanline's D disparities occupy D / (8 c) lanes
+ * (rounded up to a power of two), so a warp walks more scanlines at once and
+ * reduces each one's minimum with fewer shuffles.  Results do not depend on
+ * either setting.  A new handle starts with 3 blocks per SM and 1 chunk per
+ * lane, or with what sgm_autotune chose for its shape. */
+int sgm_set_aggregation(sgm_handle h, int blocks_per_sm, int chunks_per_lane);
+int sgm_get_aggregation(sgm_handle h, int *blocks_per_sm, int *chunks_per_lane);
 
 /* Path schedules: how the aggregation of Eq. 2 is organised on the GPU.
  *   PLANES: every enabled direction is cut into independent scanlines that
@@ -260,7 +274,8 @@ int sgm_get_schedule(sgm_handle h, int *schedule, int *rows_per_cta);
 
 /* Autotuner: times the pipeline on this pair (device pointers as for
  * sgm_compute; disp is overwritten) with the PLANES schedule at 1, 2, 3, 4
- * and 6 resident aggregation blocks per SM and, where h can run it, the SWEEP
+ * and 6 resident aggregation blocks per SM, each with 1, 2 and 4 chunks per
+ * lane where D allows (sgm_set_aggregation), and, where h can run it, the SWEEP
  * schedule at 2, 4 and 8 rows per block; keeps the fastest for h and for
  * handles created later in this process with the same W, H, D, path mask,
  * cost, window and P2.  *best_blocks_per_sm (may be NULL) receives the best

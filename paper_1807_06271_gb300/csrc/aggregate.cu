@@ -51,15 +51,14 @@
 // and width, with evict_first: the planes are read back only once, by the
 // WTA kernel.  16-bit path costs run through the same packed arithmetic: the
 // host keeps cmax + P2 below the 0x7FFF padding marker.
-#include <type_traits>
 
 #include "sgm_internal.cuh"
 
 namespace sgm {
 
-PathJobs make_path_jobs(int W, int H, int D, int mask) {
+PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl) {
     PathJobs j = {};
-    const int G = 32 / lanes_per_scanline(D);
+    const int G = 32 / (lanes_per_scanline(D) / cpl);
     // long axis first, then the short axis, then the diagonals
     const bool wide = W >= H;
     const int order[kMaxPaths] = {wide ? 0 : 2, wide ? 1 : 3, wide ? 2 : 0, wide ? 3 : 1, 4, 5, 6, 7};
@@ -133,56 +132,6 @@ __device__ __forceinline__ unsigned next_job(unsigned *state, unsigned nlong, un
     return jl < nlong ? jl : total;
 }
 
-// One lane's chunk of DPL disparities in memory: DPL bytes (8-bit costs) or
-// 2*DPL bytes (16-bit, "wide"), as uint2 or uint4.
-template <int DPL, bool WIDE>
-struct Lane {
-    static constexpr int kBytes = WIDE ? 2 * DPL : DPL;
-    static_assert(kBytes == 8 || kBytes == 16, "a lane chunk is 8 or 16 bytes");
-    using T = typename std::conditional<kBytes == 8, uint2, uint4>::type;
-    static constexpr int kWords = kBytes / 4;
-};
-
-__device__ __forceinline__ uint32_t word_of(const uint2 &c, int w) { return w == 0 ? c.x : c.y; }
-__device__ __forceinline__ uint32_t word_of(const uint4 &c, int w) {
-    return w == 0 ? c.x : w == 1 ? c.y : w == 2 ? c.z : c.w;
-}
-template <typename T>
-__device__ __forceinline__ T chunk_of(const uint32_t *w) {
-    if constexpr (sizeof(T) == 8) return make_uint2(w[0], w[1]);
-    else return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-template <typename T>
-__device__ __forceinline__ T ld_chunk(const T *p) {
-    T v;
-    if constexpr (sizeof(T) == 8) {
-        asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    } else {
-        asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                     : "l"(p));
-    }
-    return v;
-}
-template <typename T>
-__device__ __forceinline__ void st_chunk(T *p, const T &v, uint64_t pol) {
-    if constexpr (sizeof(T) == 8) {
-        asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p),
-                     "r"(v.x), "r"(v.y), "l"(pol)
-                     : "memory");
-    } else {
-        asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
-                     "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
-                     : "memory");
-    }
-}
-template <typename T>
-__device__ __forceinline__ T zero_chunk() {
-    const uint32_t z[4] = {0u, 0u, 0u, 0u};
-    return chunk_of<T>(z);
-}
-
 // (m, m) with m the minimum over the LPS lanes of this lane's scanline of
 // both halves of x.  The halves are folded first ((m, m) = m * 0x10001 is
 // monotonic in m, so it can be reduced as one 32-bit value).  Scanlines of up
@@ -215,106 +164,162 @@ __device__ __forceinline__ uint32_t line_min2(uint32_t x, int grp) {
     }
 }
 
-// Path state of one lane: R[k] = (L[k], L[k+h]) packed (h = DPL/2),
-// m2 = (m, m), mQ = m2 + (P2 - P1, P2 - P1).
-template <int DPL>
+// The CPL consecutive 8-disparity chunks one lane holds, as they sit in the
+// cost volume and the planes: 8 bytes per chunk for 8-bit costs, 16 for the
+// 16-bit costs of SAD.
+template <int CPL, bool WIDE>
+struct Blk {
+    static constexpr int kWords = CPL * (WIDE ? 4 : 2);
+    static_assert(kWords == 2 || kWords % 4 == 0, "a lane block is 8 bytes or whole 16-byte vectors");
+    uint32_t w[kWords];
+};
+
+template <int CPL, bool WIDE>
+__device__ __forceinline__ Blk<CPL, WIDE> ld_blk(const Blk<CPL, WIDE> *p) {
+    Blk<CPL, WIDE> v;
+    if constexpr (Blk<CPL, WIDE>::kWords == 2) {
+        asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.w[0]), "=r"(v.w[1]) : "l"(p));
+    } else {
+#pragma unroll
+        for (int q = 0; q < Blk<CPL, WIDE>::kWords; q += 4)
+            asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.w[q]), "=r"(v.w[q + 1]), "=r"(v.w[q + 2]), "=r"(v.w[q + 3])
+                         : "l"(reinterpret_cast<const uint32_t *>(p) + q));
+    }
+    return v;
+}
+template <int CPL, bool WIDE>
+__device__ __forceinline__ void st_blk(Blk<CPL, WIDE> *p, const Blk<CPL, WIDE> &v, uint64_t pol) {
+    if constexpr (Blk<CPL, WIDE>::kWords == 2) {
+        asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.w[0]),
+                     "r"(v.w[1]), "l"(pol)
+                     : "memory");
+    } else {
+#pragma unroll
+        for (int q = 0; q < Blk<CPL, WIDE>::kWords; q += 4)
+            asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(
+                             reinterpret_cast<uint32_t *>(p) + q),
+                         "r"(v.w[q]), "r"(v.w[q + 1]), "r"(v.w[q + 2]), "r"(v.w[q + 3]), "l"(pol)
+                         : "memory");
+    }
+}
+
+// Path state of one lane: chunk c holds R[c][k] = (L[d_c+k], L[d_c+k+4]) packed
+// (d_c its first disparity), m2 = (m, m), mQ = m2 + (P2 - P1, P2 - P1).
+template <int CPL>
 struct PathState {
-    uint32_t R[DPL / 2];
+    uint32_t R[CPL][4];
     uint32_t m2, mQ;
 };
 
-// One step of Eq. 2 for the lane's DPL disparities with cost chunk c.
-template <int LPS, int DPL, bool WIDE, bool RAGGED>
-__device__ __forceinline__ void path_step(PathState<DPL> &st, const typename Lane<DPL, WIDE>::T &c,
-                                          uint32_t P1x2, uint32_t QPx2, int grp, uint32_t lo_edge,
-                                          uint32_t hi_edge, const uint32_t (&inv)[DPL / 2]) {
-    constexpr int NR = DPL / 2;
-    uint32_t cc[NR];
-    if constexpr (WIDE) {
+// One step of Eq. 2 for the lane's CPL chunks with cost block b.  Inside a
+// chunk the d-1 / d+1 neighbours of the inner words are the neighbouring
+// words; the first and last words take their outer neighbour from the
+// previous / next chunk, which is in the same lane except at the lane's ends
+// (one shuffle each way per step, whatever CPL is).
+template <int LPS, int CPL, bool WIDE, bool RAGGED>
+__device__ __forceinline__ void path_step(PathState<CPL> &st, const Blk<CPL, WIDE> &b, uint32_t P1x2,
+                                          uint32_t QPx2, int grp, uint32_t lo_edge, uint32_t hi_edge,
+                                          const uint32_t (&inv)[CPL][4]) {
+    uint32_t cc[CPL][4];
 #pragma unroll
-        for (int k = 0; k < NR; k++) cc[k] = word_of(c, k);  // (C[k], C[k+h]) as stored
-    } else {
+    for (int c = 0; c < CPL; c++) {
+        if constexpr (WIDE) {
 #pragma unroll
-        for (int w = 0; w < DPL / 4; w++) {
-            const uint32_t v = word_of(c, w);
-            cc[2 * w] = v & kLo;                         // bytes 0, 2
-            cc[2 * w + 1] = __byte_perm(v, 0u, 0x4341);  // bytes 1, 3
+            for (int k = 0; k < 4; k++) cc[c][k] = b.w[4 * c + k];  // (C[k], C[k+4]) as stored
+        } else {
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
+                const uint32_t v = b.w[2 * c + w];
+                cc[c][2 * w] = v & kLo;                         // bytes 0, 2
+                cc[c][2 * w + 1] = __byte_perm(v, 0u, 0x4341);  // bytes 1, 3
+            }
         }
     }
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, st.R[NR - 1], 1);
-    const uint32_t next = __shfl_down_sync(0xffffffffu, st.R[0], 1);
-    // (L[-1], L[h-1]) and (L[h], L[DPL]); the first/last lane of a scanline ORs
-    // in 0x7FFF for the missing neighbour (lo_edge / hi_edge are 0 elsewhere)
-    const uint32_t dm0 = __byte_perm(prev, st.R[NR - 1], 0x5432) | lo_edge;
-    const uint32_t dpN = __byte_perm(st.R[0], next, 0x5432) | hi_edge;
-    uint32_t n[NR];
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, st.R[CPL - 1][3], 1);
+    const uint32_t next = __shfl_down_sync(0xffffffffu, st.R[0][0], 1);
+    uint32_t n[CPL][4];
 #pragma unroll
-    for (int k = 0; k < NR; k++) {
-        const uint32_t lm = k == 0 ? dm0 : st.R[k - 1];
-        const uint32_t rm = k == NR - 1 ? dpN : st.R[k + 1];
-        // min(L(d-1) + P1, L(d+1) + P1, m + P2, L(d)) as min(min(L(d-1), L(d+1),
-        // m + P2 - P1) + P1, L(d)): a three-way packed minimum and a packed
-        // add-then-minimum (the dynamic-programming instructions of sm_90+);
-        // no half wraps, as every value stays below 0x7FFF + P1
-        n[k] = __viaddmin_u16x2(__vimin3_u16x2(lm, rm, st.mQ), P1x2, st.R[k]) + cc[k] - st.m2;
-        if (RAGGED) n[k] = vmax2(n[k], inv[k]);
-    }
-    uint32_t mn = n[0];
+    for (int c = 0; c < CPL; c++) {
+        // (L[d_c-1], L[d_c+3]) and (L[d_c+4], L[d_c+8]); the first/last lane of a
+        // scanline ORs in 0x7FFF for the missing neighbour (lo_edge / hi_edge are 0 elsewhere)
+        const uint32_t dm0 = __byte_perm(c == 0 ? prev : st.R[c - 1][3], st.R[c][3], 0x5432) | (c == 0 ? lo_edge : 0u);
+        const uint32_t dpN =
+            __byte_perm(st.R[c][0], c == CPL - 1 ? next : st.R[c + 1][0], 0x5432) | (c == CPL - 1 ? hi_edge : 0u);
 #pragma unroll
-    for (int k = 0; k < NR; k++) {
-        st.R[k] = n[k];
-        if (k) mn = vmin2(mn, n[k]);
+        for (int k = 0; k < 4; k++) {
+            const uint32_t lm = k == 0 ? dm0 : st.R[c][k - 1];
+            const uint32_t rm = k == 3 ? dpN : st.R[c][k + 1];
+            // min(L(d-1) + P1, L(d+1) + P1, m + P2, L(d)) as min(min(L(d-1), L(d+1),
+            // m + P2 - P1) + P1, L(d)): a three-way packed minimum and a packed
+            // add-then-minimum (the dynamic-programming instructions of sm_90+);
+            // no half wraps, as every value stays below 0x7FFF + P1
+            n[c][k] = __viaddmin_u16x2(__vimin3_u16x2(lm, rm, st.mQ), P1x2, st.R[c][k]) + cc[c][k] - st.m2;
+            if (RAGGED) n[c][k] = vmax2(n[c][k], inv[c][k]);
+        }
     }
+    // lane minimum: three-way minima over the lane's words
+    uint32_t mc[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; c++) mc[c] = vmin2(__vimin3_u16x2(n[c][0], n[c][1], n[c][2]), n[c][3]);
+    uint32_t mn = mc[0];
+#pragma unroll
+    for (int c = 1; c < CPL; c += 2) mn = c + 1 < CPL ? __vimin3_u16x2(mn, mc[c], mc[c + 1]) : vmin2(mn, mc[c]);
+#pragma unroll
+    for (int c = 0; c < CPL; c++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) st.R[c][k] = n[c][k];
     st.m2 = line_min2<LPS>(mn, grp);
     st.mQ = st.m2 + QPx2;
 }
 
-// The lane's DPL path costs in the cost volume's order.  Padding slots
-// (0x7FFF) are stored as their low byte (8-bit) or as 0 (16-bit), so that sums
-// over the planes never carry out of a 16-bit half; no WTA key uses them.
-template <int DPL, bool WIDE, bool RAGGED>
-__device__ __forceinline__ typename Lane<DPL, WIDE>::T pack_plane(const PathState<DPL> &st,
-                                                                  const uint32_t (&inv)[DPL / 2]) {
-    using CT = typename Lane<DPL, WIDE>::T;
-    uint32_t w[Lane<DPL, WIDE>::kWords];
-    if constexpr (WIDE) {
+// The lane's path costs in the cost volume's order.  Padding slots (0x7FFF)
+// are stored as their low byte (8-bit) or as 0 (16-bit), so that sums over
+// the planes never carry out of a 16-bit half; no WTA key uses them.
+template <int CPL, bool WIDE, bool RAGGED>
+__device__ __forceinline__ Blk<CPL, WIDE> pack_plane(const PathState<CPL> &st, const uint32_t (&inv)[CPL][4]) {
+    Blk<CPL, WIDE> b;
 #pragma unroll
-        for (int k = 0; k < DPL / 2; k++) w[k] = RAGGED ? st.R[k] & ~inv[k] : st.R[k];
-    } else {
+    for (int c = 0; c < CPL; c++) {
+        if constexpr (WIDE) {
 #pragma unroll
-        for (int i = 0; i < DPL / 4; i++) {
-            uint32_t a = st.R[2 * i], b = st.R[2 * i + 1];
-            if (RAGGED) {
-                a &= kLo;
-                b &= kLo;
+            for (int k = 0; k < 4; k++) b.w[4 * c + k] = RAGGED ? st.R[c][k] & ~inv[c][k] : st.R[c][k];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                uint32_t lo = st.R[c][2 * i], hi = st.R[c][2 * i + 1];
+                if (RAGGED) {
+                    lo &= kLo;
+                    hi &= kLo;
+                }
+                b.w[2 * c + i] = hi * 256u + lo;
             }
-            w[i] = b * 256u + a;
         }
     }
-    return chunk_of<CT>(w);
+    return b;
 }
 
 // One job: the G neighbouring scanlines s0 .. s0+G-1 of one direction
 // (dx, dy), scanline s0 + grp for this lane's group, written to plane
-// `plane` of `nplanes`.
-template <int LPS, int DPL, bool WIDE, bool RAGGED, int PF>
-__device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__restrict__ cost,
-                                        typename Lane<DPL, WIDE>::T *__restrict__ planes, int W, int H, int D,
-                                        int nplanes, int dx, int dy, int plane, int nlines, int s0,
-                                        uint32_t P1x2, uint32_t P2x2, uint64_t pol_stream) {
-    using CT = typename Lane<DPL, WIDE>::T;
-    constexpr int NR = DPL / 2;
+// `plane` of `nplanes`.  A scanline's pixel holds LPS lane blocks of CPL
+// chunks each.
+template <int LPS, int CPL, bool WIDE, bool RAGGED, int PF>
+__device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost, Blk<CPL, WIDE> *__restrict__ planes,
+                                        int W, int H, int D, int nplanes, int dx, int dy, int plane, int nlines,
+                                        int s0, uint32_t P1x2, uint32_t P2x2, uint64_t pol_stream) {
+    using BT = Blk<CPL, WIDE>;
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPS, li = lane % LPS;
     const uint32_t lo_edge = li == 0 ? 0x7FFFu : 0u;            // no d = -1
     const uint32_t hi_edge = li == LPS - 1 ? 0x7FFF0000u : 0u;  // no d = Dp
-    uint32_t inv[NR];
+    uint32_t inv[CPL][4];
 #pragma unroll
-    for (int k = 0; k < NR; k++) {
-        inv[k] = 0u;
-        if (RAGGED)
-            inv[k] = (DPL * li + k >= D ? 0x7FFFu : 0u) | (DPL * li + k + NR >= D ? 0x7FFF0000u : 0u);
-    }
+    for (int c = 0; c < CPL; c++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int d = (li * CPL + c) * 8 + k;
+            inv[c][k] = RAGGED ? ((d >= D ? 0x7FFFu : 0u) | (d + 4 >= D ? 0x7FFF0000u : 0u)) : 0u;
+        }
     const int s = s0 + grp;
     int x = 0, y = 0, len = 0;
     if (s < nlines) {
@@ -338,25 +343,33 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
         }
     }
     const int steps = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
-    // chunk indices: cost chunk (x, y, li) is cost[(y*W + x)*LPS + li], plane
-    // chunk is planes[((y*W + x)*nplanes + plane)*LPS + li] (all planes of a
+    // block indices: cost block (x, y, li) is cost[(y*W + x)*LPS + li], plane
+    // block is planes[((y*W + x)*nplanes + plane)*LPS + li] (all planes of a
     // pixel are adjacent).  Indices stay below 2^31 (checked at handle creation).
     const int pix = y * W + x;
     const int cstep = (dy * W + dx) * LPS;
     const int ostep = cstep * nplanes;
-    int ci_ld = pix * LPS + li;  // next cost chunk to load into the ring
+    int ci_ld = pix * LPS + li;  // next cost block to load into the ring
     int oi = (pix * nplanes + plane) * LPS + li;
-    CT ring[PF];
+    BT ring[PF];
 #pragma unroll
     for (int i = 0; i < PF; i++) {
-        ring[i] = i < len ? ld_chunk(cost + ci_ld) : zero_chunk<CT>();
+        if (i < len) {
+            ring[i] = ld_blk(cost + ci_ld);
+        } else {
+#pragma unroll
+            for (int q = 0; q < BT::kWords; q++) ring[i].w[q] = 0u;
+        }
         ci_ld += cstep;
     }
-    PathState<DPL> st;
+    PathState<CPL> st;
 #pragma unroll
-    for (int q = 0; q < NR; q++) st.R[q] = inv[q];
+    for (int c = 0; c < CPL; c++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) st.R[c][k] = inv[c][k];
     st.m2 = 0u;
     st.mQ = P2x2 - P1x2;
+    const uint32_t QPx2 = P2x2 - P1x2;
     int rem = len;  // steps of this lane's scanline not yet taken
     int t0 = 0;
     // While every scanline of the warp has at least 2 * PF steps left, the
@@ -365,11 +378,11 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
     for (; t0 + 2 * PF <= minlen; t0 += PF) {
 #pragma unroll
         for (int i = 0; i < PF; i++) {
-            const CT c = ring[i];
-            ring[i] = ld_chunk(cost + ci_ld);
+            const BT c = ring[i];
+            ring[i] = ld_blk(cost + ci_ld);
             ci_ld += cstep;
-            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2 - P1x2, grp, lo_edge, hi_edge, inv);
-            st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
+            path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv);
+            st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv), pol_stream);
             oi += ostep;
         }
         rem -= PF;
@@ -377,11 +390,11 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
     for (; t0 + PF <= steps; t0 += PF) {
 #pragma unroll
         for (int i = 0; i < PF; i++) {
-            const CT c = ring[i];
-            if (rem > PF) ring[i] = ld_chunk(cost + ci_ld);
+            const BT c = ring[i];
+            if (rem > PF) ring[i] = ld_blk(cost + ci_ld);
             ci_ld += cstep;
-            path_step<LPS, DPL, WIDE, RAGGED>(st, c, P1x2, P2x2 - P1x2, grp, lo_edge, hi_edge, inv);
-            if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
+            path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv);
+            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv), pol_stream);
             oi += ostep;
             rem--;
         }
@@ -389,19 +402,18 @@ __device__ __forceinline__ void run_job(const typename Lane<DPL, WIDE>::T *__res
 #pragma unroll
     for (int i = 0; i < PF; i++) {  // the last steps < PF
         if (t0 + i < steps) {
-            path_step<LPS, DPL, WIDE, RAGGED>(st, ring[i], P1x2, P2x2 - P1x2, grp, lo_edge, hi_edge, inv);
-            if (rem > 0) st_chunk(planes + oi, pack_plane<DPL, WIDE, RAGGED>(st, inv), pol_stream);
+            path_step<LPS, CPL, WIDE, RAGGED>(st, ring[i], P1x2, QPx2, grp, lo_edge, hi_edge, inv);
+            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv), pol_stream);
             oi += ostep;
             rem--;
         }
     }
 }
 
-template <int LPS, int DPL, bool WIDE, bool RAGGED, int PF>
+template <int LPS, int CPL, bool WIDE, bool RAGGED, int PF>
 __global__ void __launch_bounds__(kWarps * 32)
-    aggregate_kernel(const typename Lane<DPL, WIDE>::T *__restrict__ cost, int W, int H, int D,
-                     uint32_t P1x2, uint32_t P2x2, PathJobs jobs,
-                     typename Lane<DPL, WIDE>::T *__restrict__ planes, int nplanes,
+    aggregate_kernel(const Blk<CPL, WIDE> *__restrict__ cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
+                     PathJobs jobs, Blk<CPL, WIDE> *__restrict__ planes, int nplanes,
                      unsigned *__restrict__ job_counter) {
     wait_for_predecessor();
     constexpr int G = 32 / LPS;
@@ -417,7 +429,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (job >= (unsigned)total) return;
         int k = 0;
         while ((int)job >= jobs.jbegin[k + 1]) k++;
-        run_job<LPS, DPL, WIDE, RAGGED, PF>(cost, planes, W, H, D, nplanes, jobs.dx[k], jobs.dy[k], jobs.plane[k],
+        run_job<LPS, CPL, WIDE, RAGGED, PF>(cost, planes, W, H, D, nplanes, jobs.dx[k], jobs.dy[k], jobs.plane[k],
                                             jobs.nlines[k], ((int)job - jobs.jbegin[k]) * G, P1x2, P2x2, pol_stream);
     }
 }
@@ -426,7 +438,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 // PathJobs; the two queues number all pairs' long-axis jobs (queue 0) and
 // all their other jobs (queue 1) in pair order, pair p's starting at
 // pfx[0][p] and pfx[1][p].  Each job runs with its pair's lanes per scanline.
-template <int DPL, bool WIDE, int PF>
+template <int CPL, bool WIDE, int PF>
 __global__ void __launch_bounds__(kWarps * 32)
     aggregate_batch_kernel(const BatchAggPair *__restrict__ pairs, int npairs, const int *__restrict__ prefix,
                            uint32_t P1x2, uint32_t P2x2, unsigned *__restrict__ job_counter) {
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     extern __shared__ int spfx[];  // [2][npairs + 1]
     for (int i = threadIdx.x; i < 2 * (npairs + 1); i += blockDim.x) spfx[i] = prefix[i];
     __syncthreads();
-    using CT = typename Lane<DPL, WIDE>::T;
+    using BT = Blk<CPL, WIDE>;
     const int lane = threadIdx.x & 31;
     const int nlong = spfx[npairs], nother = spfx[npairs + 1 + npairs];
     const int total = nlong + nother;
@@ -462,10 +474,10 @@ __global__ void __launch_bounds__(kWarps * 32)
         while (local >= p.jobs.jbegin[k + 1]) k++;
         const int G = 32 / p.lps;
         const int s0 = (local - p.jobs.jbegin[k]) * G;
-        const CT *cost = reinterpret_cast<const CT *>(p.cost);
-        CT *planes = reinterpret_cast<CT *>(p.planes);
+        const BT *cost = reinterpret_cast<const BT *>(p.cost);
+        BT *planes = reinterpret_cast<BT *>(p.planes);
 #define SGM_JOB(L, RG)                                                                                      \
-    run_job<L, DPL, WIDE, RG, PF>(cost, planes, p.W, p.H, p.D, p.nplanes, p.jobs.dx[k], p.jobs.dy[k],       \
+    run_job<L, CPL, WIDE, RG, PF>(cost, planes, p.W, p.H, p.D, p.nplanes, p.jobs.dx[k], p.jobs.dy[k],       \
                                   p.jobs.plane[k], p.jobs.nlines[k], s0, P1x2, P2x2, pol_stream)
 #define SGM_JOB_L(L)              \
     if (p.ragged) SGM_JOB(L, true); \
@@ -475,40 +487,46 @@ __global__ void __launch_bounds__(kWarps * 32)
             case 2: SGM_JOB_L(2); break;
             case 4: SGM_JOB_L(4); break;
             case 8: SGM_JOB_L(8); break;
-            case 16: SGM_JOB_L(16); break;
-            default: SGM_JOB_L(32); break;
+            case 16: if (CPL <= 2) SGM_JOB_L(16); break;
+            default: if (CPL == 1) SGM_JOB_L(32); break;
         }
 #undef SGM_JOB_L
 #undef SGM_JOB
     }
 }
 
-template <int LPS, int DPL, bool WIDE>
+// Cost blocks loaded PF steps ahead: 16 for 8-byte blocks, 8 for 16- and 32-byte ones.
+template <int CPL, bool WIDE>
+constexpr int prefetch_depth() {
+    return Blk<CPL, WIDE>::kWords == 2 ? 16 : 8;
+}
+
+template <int LPS, int CPL, bool WIDE>
 cudaError_t launch_lps(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                        const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
                        int blocks, cudaStream_t s) {
-    using CT = typename Lane<DPL, WIDE>::T;
-    // cost loads issued PF steps ahead: 16 chunks of 8 bytes, 8 of 16 bytes
-    constexpr int PF = sizeof(CT) == 8 ? 16 : 8;
-    const CT *c = reinterpret_cast<const CT *>(cost);
-    CT *p = reinterpret_cast<CT *>(planes);
-    auto kernel = D == DPL * LPS ? aggregate_kernel<LPS, DPL, WIDE, false, PF> : aggregate_kernel<LPS, DPL, WIDE, true, PF>;
+    using BT = Blk<CPL, WIDE>;
+    constexpr int PF = prefetch_depth<CPL, WIDE>();
+    const BT *c = reinterpret_cast<const BT *>(cost);
+    BT *p = reinterpret_cast<BT *>(planes);
+    auto kernel = D == 8 * CPL * LPS ? aggregate_kernel<LPS, CPL, WIDE, false, PF>
+                                     : aggregate_kernel<LPS, CPL, WIDE, true, PF>;
     return launch_k(kernel, dim3(blocks), dim3(kWarps * 32), 0, s, c, W, H, D, P1x2, P2x2, jobs, p, nplanes,
                     job_counter);
 }
 
-template <bool WIDE>
-cudaError_t launch_all(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
+template <int CPL, bool WIDE>
+cudaError_t launch_cpl(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                        const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
                        int blocks, cudaStream_t s) {
-#define SGM_AGG(L) launch_lps<L, 8, WIDE>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s)
-    switch (lanes_per_scanline(D)) {
+#define SGM_AGG(L) launch_lps<L, CPL, WIDE>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s)
+    switch (lanes_per_scanline(D) / CPL) {
         case 1: return SGM_AGG(1);
         case 2: return SGM_AGG(2);
         case 4: return SGM_AGG(4);
         case 8: return SGM_AGG(8);
-        case 16: return SGM_AGG(16);
-        default: return SGM_AGG(32);
+        case 16: if constexpr (CPL <= 2) return SGM_AGG(16); else return cudaErrorInvalidValue;
+        default: if constexpr (CPL == 1) return SGM_AGG(32); else return cudaErrorInvalidValue;
     }
 #undef SGM_AGG
 }
@@ -533,23 +551,32 @@ __global__ void unpermute_kernel(const uint8_t *__restrict__ plane, int npx, int
 
 }  // namespace
 
+int chunks_per_lane_max(int D, bool wide) {
+    const int chunks = lanes_per_scanline(D);  // 8-disparity chunks per pixel
+    return wide ? 1 : (chunks >= 4 ? 4 : chunks);
+}
+
 cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2, bool wide,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
-                             unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
+                             unsigned *job_counter, int blocks_per_sm, int cpl, cudaStream_t s) {
     if (jobs.jbegin[jobs.n] == 0) return cudaSuccess;
     if (disparities_per_lane(D) != 8) return cudaErrorInvalidValue;
+    if (cpl != 1 && cpl != 2 && cpl != 4) return cudaErrorInvalidValue;
+    if (cpl > chunks_per_lane_max(D, wide)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int blocks = sms * (blocks_per_sm > 0 ? blocks_per_sm : 2);
     const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
-    if (wide) return launch_all<true>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
-    return launch_all<false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+    if (wide) return launch_cpl<1, true>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+    if (cpl == 4) return launch_cpl<4, false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+    if (cpl == 2) return launch_cpl<2, false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+    return launch_cpl<1, false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
 }
 
 cudaError_t launch_aggregate_batch(const BatchAggPair *pairs, int npairs, const int *prefix, int P1, int P2,
-                                   bool wide, unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
+                                   bool wide, int cpl, unsigned *job_counter, int blocks_per_sm, cudaStream_t s) {
     if (npairs <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -559,10 +586,13 @@ cudaError_t launch_aggregate_batch(const BatchAggPair *pairs, int npairs, const 
     const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
     const size_t smem = sizeof(int) * 2 * (size_t)(npairs + 1);
     if (wide)
-        return launch_k(aggregate_batch_kernel<8, true, 8>, dim3(blocks), dim3(kWarps * 32), smem, s, pairs, npairs,
-                        prefix, P1x2, P2x2, job_counter);
-    return launch_k(aggregate_batch_kernel<8, false, 16>, dim3(blocks), dim3(kWarps * 32), smem, s, pairs, npairs,
-                    prefix, P1x2, P2x2, job_counter);
+        return launch_k(aggregate_batch_kernel<1, true, prefetch_depth<1, true>()>, dim3(blocks), dim3(kWarps * 32),
+                        smem, s, pairs, npairs, prefix, P1x2, P2x2, job_counter);
+    if (cpl == 4)
+        return launch_k(aggregate_batch_kernel<4, false, prefetch_depth<4, false>()>, dim3(blocks), dim3(kWarps * 32),
+                        smem, s, pairs, npairs, prefix, P1x2, P2x2, job_counter);
+    return launch_k(aggregate_batch_kernel<1, false, prefetch_depth<1, false>()>, dim3(blocks), dim3(kWarps * 32),
+                    smem, s, pairs, npairs, prefix, P1x2, P2x2, job_counter);
 }
 
 cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,

@@ -86,7 +86,7 @@ sgm::Tuning sgm::tuned_for(const sgm_handle_s *h) {
     const TuneKey k = tune_key(h);
     for (auto &e : g_tuned)
         if (e.first == k) return e.second;
-    return Tuning{0, SGM_SCHEDULE_PLANES, 4};
+    return Tuning{0, SGM_SCHEDULE_PLANES, 4, 1};
 }
 
 extern "C" int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *const *left,
@@ -114,7 +114,7 @@ extern "C" int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *con
         rc = run_forked(n, hs, left, right, disp, umap, vmap, s);
     } else {
         BatchKey key;
-        key.v.reserve(8 * n);
+        key.v.reserve(9 * n);
         for (int i = 0; i < n; i++) {
             key.v.push_back(hs[i]);
             key.v.push_back(left[i]);
@@ -124,6 +124,7 @@ extern "C" int sgm_batch_compute(int n, const sgm_handle *hs, const uint8_t *con
             key.v.push_back(umap && vmap ? (const void *)vmap[i] : nullptr);
             key.v.push_back((const void *)(intptr_t)hs[i]->agg_blocks_per_sm);
             key.v.push_back((const void *)(intptr_t)(hs[i]->schedule * 64 + hs[i]->sweep_rows));
+            key.v.push_back((const void *)(intptr_t)hs[i]->agg_cpl);
         }
         std::lock_guard<std::mutex> lock(g_mu);
         BatchGraph *hit = nullptr;
@@ -181,26 +182,34 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = SGM_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SGM_ERR_CUDA;
-    const int saved = h->agg_blocks_per_sm, saved_timing = h->timing;
+    const int saved = h->agg_blocks_per_sm, saved_timing = h->timing, saved_cpl = h->agg_cpl;
     const int saved_schedule = h->schedule, saved_rows = h->sweep_rows;
     h->timing = 0;
-    // candidates: the plane schedule at each resident-block count, then the
-    // fused sweep at each rows-per-CTA count it can run with
+    // candidates: the plane schedule at each resident-block count and each
+    // number of chunks per lane, then the fused sweep at each rows-per-CTA
+    // count it can run with
     struct Cand {
-        int schedule, param;
+        int schedule, param, cpl;
     };
     std::vector<Cand> cands;
-    for (int c : {1, 2, 3, 4, 6}) cands.push_back({SGM_SCHEDULE_PLANES, c});
+    const int cmax = sgm::chunks_per_lane_max(h->D, h->wide != 0);
+    for (int cpl : {1, 2, 4})
+        if (cpl <= cmax)
+            for (int c : {1, 2, 3, 4, 6}) cands.push_back({SGM_SCHEDULE_PLANES, c, cpl});
     for (int r : {2, 4, 8})
-        if (sgm::sweep_feasible(h, r) == SGM_OK) cands.push_back({SGM_SCHEDULE_SWEEP, r});
-    int best_bps = saved;
-    Cand best{saved_schedule, saved_schedule == SGM_SCHEDULE_SWEEP ? saved_rows : saved};
+        if (sgm::sweep_feasible(h, r) == SGM_OK) cands.push_back({SGM_SCHEDULE_SWEEP, r, saved_cpl});
+    int best_bps = saved, best_cpl = saved_cpl;
+    Cand best{saved_schedule, saved_schedule == SGM_SCHEDULE_SWEEP ? saved_rows : saved, saved_cpl};
     float best_ms = 1e30f, best_planes_ms = 1e30f;
     for (const Cand &c : cands) {
         if (rc != SGM_OK) break;
         h->schedule = c.schedule;
-        if (c.schedule == SGM_SCHEDULE_SWEEP) h->sweep_rows = c.param;
-        else h->agg_blocks_per_sm = c.param;
+        if (c.schedule == SGM_SCHEDULE_SWEEP) {
+            h->sweep_rows = c.param;
+        } else {
+            h->agg_blocks_per_sm = c.param;
+            h->agg_cpl = c.cpl;
+        }
         for (int w = 0; w < 2 && rc == SGM_OK; w++)
             rc = sgm::compute_pair(h, left, right, disp, nullptr, nullptr, s);
         if (rc != SGM_OK) break;
@@ -214,6 +223,7 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
         if (rc == SGM_OK && c.schedule == SGM_SCHEDULE_PLANES && ms < best_planes_ms) {
             best_planes_ms = ms;
             best_bps = c.param;
+            best_cpl = c.cpl;
         }
         if (rc == SGM_OK && ms < best_ms) {
             best_ms = ms;
@@ -223,10 +233,12 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
     h->timing = saved_timing;
     if (rc == SGM_OK) {
         h->agg_blocks_per_sm = best_bps;
+        h->agg_cpl = best_cpl;
         h->schedule = best.schedule;
         h->sweep_rows = best.schedule == SGM_SCHEDULE_SWEEP ? best.param : saved_rows;
     } else {
         h->agg_blocks_per_sm = saved;
+        h->agg_cpl = saved_cpl;
         h->schedule = saved_schedule;
         h->sweep_rows = saved_rows;
     }
@@ -234,7 +246,7 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
     if (rc == SGM_OK) {
         std::lock_guard<std::mutex> lock(g_mu);
         const TuneKey k = tune_key(h);
-        const sgm::Tuning t{best_bps, h->schedule, h->sweep_rows};
+        const sgm::Tuning t{best_bps, h->schedule, h->sweep_rows, best_cpl};
         bool found = false;
         for (auto &e : g_tuned)
             if (e.first == k) {

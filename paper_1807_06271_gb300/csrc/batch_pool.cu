@@ -52,6 +52,8 @@ struct sgm_batch_s {
     std::vector<PairSlot> pairs;
     std::vector<Group> groups;
     int ngroups, blocks_per_sm;
+    int cpl;      // chunks per lane of the batched aggregation (1 or 4)
+    int cpl_max;  // 4 when every pair allows it, else 1
     unsigned char *pool;
     size_t pool_bytes;  // the whole pool
     size_t tables_at;   // where the group tables start (after the pairs' scratch)
@@ -124,10 +126,10 @@ int layout_groups(sgm_batch_s *b, int ng, bool upload, size_t at, size_t *end) {
             t.W = ps.W;
             t.H = ps.H;
             t.D = ps.D;
-            t.lps = lanes_per_scanline(ps.D);
-            t.ragged = ps.D != 8 * t.lps;
+            t.lps = lanes_per_scanline(ps.D) / b->cpl;
+            t.ragged = ps.D != 8 * lanes_per_scanline(ps.D);
             t.nplanes = b->npaths;
-            t.jobs = make_path_jobs(ps.W, ps.H, ps.D, b->p.path_mask);
+            t.jobs = make_path_jobs(ps.W, ps.H, ps.D, b->p.path_mask, b->cpl);
             prefix[k + 1] = prefix[k] + t.jobs.nlong;
             prefix[np + 1 + k + 1] = prefix[np + 1 + k] + (t.jobs.jbegin[t.jobs.n] - t.jobs.nlong);
         }
@@ -187,7 +189,7 @@ int enqueue(sgm_batch_s *b, const uint8_t *const *left, const uint8_t *const *ri
         if (cudaMemsetAsync(b->pool + g.job_state, 0, kJobStateBytes, g.stream) != cudaSuccess ||
             launch_aggregate_batch(reinterpret_cast<const BatchAggPair *>(b->pool + g.table), (int)g.pairs.size(),
                                    reinterpret_cast<const int *>(b->pool + g.prefix), b->p.P1, b->p.P2, b->wide != 0,
-                                   reinterpret_cast<unsigned *>(b->pool + g.job_state), b->blocks_per_sm,
+                                   b->cpl, reinterpret_cast<unsigned *>(b->pool + g.job_state), b->blocks_per_sm,
                                    g.stream) != cudaSuccess ||
             cudaEventRecord(g.aggregated, g.stream) != cudaSuccess)
             return SGM_ERR_CUDA;
@@ -272,6 +274,10 @@ int sgm_batch_create(int n, const int *W, const int *H, const int *D, const sgm_
     b->npaths = __builtin_popcount((unsigned)params->path_mask);
     b->ngroups = 1;
     b->blocks_per_sm = 3;
+    b->cpl = 1;
+    b->cpl_max = 4;
+    for (int i = 0; i < n; i++)
+        if (chunks_per_lane_max(D[i], b->wide != 0) < 4) b->cpl_max = 1;
     if (cudaGetDevice(&b->device) != cudaSuccess) {
         delete b;
         cudaGetLastError();
@@ -339,18 +345,22 @@ int sgm_batch_device_bytes(sgm_batch b, size_t *bytes) {
     return SGM_OK;
 }
 
-int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm) {
+int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm, int chunks_per_lane) {
     if (!b || groups < 1 || groups > kMaxGroups || (groups & (groups - 1)) || blocks_per_sm < 1 || blocks_per_sm > 16)
         return SGM_ERR_INVALID_ARG;
+    if (chunks_per_lane != 1 && chunks_per_lane != 4) return SGM_ERR_INVALID_ARG;
+    if (chunks_per_lane > b->cpl_max) return SGM_ERR_UNSUPPORTED;
     DeviceSwitch on(b->device);
     if (!on.ok) return SGM_ERR_CUDA;
     const int ng = std::min(groups, b->n);
-    if (ng != b->ngroups) {
+    if (ng != b->ngroups || chunks_per_lane != b->cpl) {
         // the tables are rewritten in place: nothing of b may still run
         if (cudaDeviceSynchronize() != cudaSuccess) {
             cudaGetLastError();
             return SGM_ERR_CUDA;
         }
+        b->cpl = chunks_per_lane;
+        b->ngroups = 0;  // force the rebuild
         const int rc = regroup(b, ng);
         if (rc != SGM_OK) return rc;
     }
@@ -358,10 +368,11 @@ int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm) {
     return SGM_OK;
 }
 
-int sgm_batch_get_tuning(sgm_batch b, int *groups, int *blocks_per_sm) {
+int sgm_batch_get_tuning(sgm_batch b, int *groups, int *blocks_per_sm, int *chunks_per_lane) {
     if (!b) return SGM_ERR_INVALID_ARG;
     if (groups) *groups = b->ngroups;
     if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+    if (chunks_per_lane) *chunks_per_lane = b->cpl;
     return SGM_OK;
 }
 
@@ -384,6 +395,7 @@ int sgm_batch_run(sgm_batch b, const uint8_t *const *left, const uint8_t *const 
     }
     key.push_back((const void *)(intptr_t)b->ngroups);
     key.push_back((const void *)(intptr_t)b->blocks_per_sm);
+    key.push_back((const void *)(intptr_t)b->cpl);
     if (!b->exec || key != b->key) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -415,7 +427,7 @@ int sgm_batch_run(sgm_batch b, const uint8_t *const *left, const uint8_t *const 
 
 int sgm_batch_autotune(sgm_batch b, const uint8_t *const *left, const uint8_t *const *right, uint8_t *const *disp,
                        uint16_t *const *umap, uint16_t *const *vmap, void *stream, int *best_groups,
-                       int *best_blocks_per_sm) {
+                       int *best_blocks_per_sm, int *best_chunks_per_lane) {
     if (!b) return SGM_ERR_INVALID_ARG;
     int rc = check_buffers(b, left, right, disp, umap, vmap);
     if (rc != SGM_OK) return rc;
@@ -424,33 +436,38 @@ int sgm_batch_autotune(sgm_batch b, const uint8_t *const *left, const uint8_t *c
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SGM_ERR_CUDA;
-    int bg = b->ngroups, bb = b->blocks_per_sm;
+    int bg = b->ngroups, bb = b->blocks_per_sm, bc = b->cpl;
     float best = 1e30f;
-    for (int g = 1; g <= kMaxGroups && rc == SGM_OK; g *= 2) {
-        if (g > 1 && (g >> 1) >= b->n) break;  // beyond one group per pair
-        for (int bps : {2, 3, 4}) {
-            rc = sgm_batch_set_tuning(b, g, bps);
-            for (int w = 0; w < 2 && rc == SGM_OK; w++) rc = sgm_batch_run(b, left, right, disp, umap, vmap, stream);
-            if (rc != SGM_OK) break;
-            float ms = 0.f;
-            if (cudaEventRecord(e0, s) != cudaSuccess) rc = SGM_ERR_CUDA;
-            for (int r = 0; r < 3 && rc == SGM_OK; r++) rc = sgm_batch_run(b, left, right, disp, umap, vmap, stream);
-            if (rc == SGM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                rc = SGM_ERR_CUDA;
-            if (rc == SGM_OK && ms < best) {
-                best = ms;
-                bg = g;
-                bb = bps;
+    for (int cpl : {1, 4}) {
+        if (cpl > b->cpl_max) break;
+        for (int g = 1; g <= kMaxGroups && rc == SGM_OK; g *= 2) {
+            if (g > 1 && (g >> 1) >= b->n) break;  // beyond one group per pair
+            for (int bps : {2, 3, 4}) {
+                rc = sgm_batch_set_tuning(b, g, bps, cpl);
+                for (int w = 0; w < 2 && rc == SGM_OK; w++) rc = sgm_batch_run(b, left, right, disp, umap, vmap, stream);
+                if (rc != SGM_OK) break;
+                float ms = 0.f;
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = SGM_ERR_CUDA;
+                for (int r = 0; r < 3 && rc == SGM_OK; r++) rc = sgm_batch_run(b, left, right, disp, umap, vmap, stream);
+                if (rc == SGM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = SGM_ERR_CUDA;
+                if (rc == SGM_OK && ms < best) {
+                    best = ms;
+                    bg = g;
+                    bb = bps;
+                    bc = cpl;
+                }
             }
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (rc == SGM_OK) rc = sgm_batch_set_tuning(b, bg, bb);
+    if (rc == SGM_OK) rc = sgm_batch_set_tuning(b, bg, bb, bc);
     if (rc == SGM_OK) {
         if (best_groups) *best_groups = b->ngroups;
         if (best_blocks_per_sm) *best_blocks_per_sm = b->blocks_per_sm;
+        if (best_chunks_per_lane) *best_chunks_per_lane = b->cpl;
     }
     cudaGetLastError();
     return rc;

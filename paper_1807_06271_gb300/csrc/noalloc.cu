@@ -146,7 +146,8 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     uint8_t *planes = base + at.planes;
     unsigned *counter = reinterpret_cast<unsigned *>(base + at.job_state);
     uint8_t *disp_lr = base + at.disp_lr;
-    const sgm::PathJobs jobs = sgm::make_path_jobs(W, H, D, params->path_mask);
+    const int cpl = sgm::chunks_per_lane_max(D, wide);
+    const sgm::PathJobs jobs = sgm::make_path_jobs(W, H, D, params->path_mask, cpl);
 
     // Every kernel below overwrites the scratch it later reads, and the cost
     // kernel clears the aggregation's work-queue state, so nothing left by an
@@ -166,7 +167,7 @@ extern "C" int sgm_compute_static(int W, int H, int D, const sgm_params *params,
     }
     if (e == cudaSuccess)
         e = sgm::launch_aggregate(cost, W, H, D, params->P1, params->P2, wide, jobs, planes, npaths,
-                                  counter, 2, s);
+                                  counter, 2, cpl, s);
     if (e == cudaSuccess)
         e = sgm::launch_wta(planes, npaths, W, H, D, wide, params->lr_tolerance, disp_lr, nullptr, nullptr,
                             nullptr, s);

@@ -142,10 +142,10 @@ int run_matching(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cud
 
 // All enabled directions into h->planes, or direction only_r alone into plane 0.
 int run_aggregate(sgm_handle_s *h, int only_r, cudaStream_t s) {
-    const PathJobs jobs = make_path_jobs(h->W, h->H, h->D, only_r >= 0 ? (1 << only_r) : h->p.path_mask);
+    const PathJobs jobs = make_path_jobs(h->W, h->H, h->D, only_r >= 0 ? (1 << only_r) : h->p.path_mask, h->agg_cpl);
     TimingRecord *t = stage_begin(h, kStageAggregate, s);
     cudaError_t e = launch_aggregate(h->cost, h->W, h->H, h->D, h->p.P1, h->p.P2, h->wide != 0, jobs, h->planes,
-                                     only_r >= 0 ? 1 : h->npaths, h->job_counter, h->agg_blocks_per_sm, s);
+                                     only_r >= 0 ? 1 : h->npaths, h->job_counter, h->agg_blocks_per_sm, h->agg_cpl, s);
     stage_end(h, t, s);
     return e == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
 }
@@ -341,11 +341,13 @@ int sgm_create(int W, int H, int D, const sgm_params *params, sgm_handle *out) {
         if ((params->path_mask >> r) & 1) h->path_of_plane[h->npaths++] = r;
     h->Dp = padded_disparities(D);
     h->agg_blocks_per_sm = 3;  // 12 resident warps per SM (fastest on 1242 x 375, D = 128)
+    h->agg_cpl = 1;  // one 8-disparity chunk per lane: fastest for single pairs on every measured shape
     h->schedule = SGM_SCHEDULE_PLANES;
     h->sweep_rows = 4;
     const Tuning tuned = tuned_for(h);
     if (tuned.blocks_per_sm > 0) {
         h->agg_blocks_per_sm = tuned.blocks_per_sm;
+        h->agg_cpl = tuned.cpl;
         h->schedule = tuned.schedule;
         h->sweep_rows = tuned.sweep_rows;
     }
@@ -752,6 +754,23 @@ int sgm_set_schedule(sgm_handle h, int schedule, int rows_per_cta) {
     h->schedule = schedule;
     if (schedule == SGM_SCHEDULE_SWEEP) h->sweep_rows = rows_per_cta;
     batch_forget(h);  // captured graphs hold the previous schedule's launches
+    return SGM_OK;
+}
+
+int sgm_set_aggregation(sgm_handle h, int blocks_per_sm, int chunks_per_lane) {
+    if (!h || blocks_per_sm < 1 || blocks_per_sm > 16) return SGM_ERR_INVALID_ARG;
+    if (chunks_per_lane != 1 && chunks_per_lane != 2 && chunks_per_lane != 4) return SGM_ERR_INVALID_ARG;
+    if (chunks_per_lane > chunks_per_lane_max(h->D, h->wide != 0)) return SGM_ERR_UNSUPPORTED;
+    h->agg_blocks_per_sm = blocks_per_sm;
+    h->agg_cpl = chunks_per_lane;
+    batch_forget(h);  // captured graphs hold the previous launch shape
+    return SGM_OK;
+}
+
+int sgm_get_aggregation(sgm_handle h, int *blocks_per_sm, int *chunks_per_lane) {
+    if (!h) return SGM_ERR_INVALID_ARG;
+    if (blocks_per_sm) *blocks_per_sm = h->agg_blocks_per_sm;
+    if (chunks_per_lane) *chunks_per_lane = h->agg_cpl;
     return SGM_OK;
 }
 

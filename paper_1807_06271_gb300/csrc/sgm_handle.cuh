@@ -62,6 +62,7 @@ struct sgm_handle_s {
     unsigned *dev_status;   // bit 0: a bounded device wait gave up (one word after the work-queue state)
     int cost_kernel;        // SGM_COST_KERNEL_* of the census cost
     int agg_blocks_per_sm;  // resident 4-warp blocks per SM of the aggregation kernel
+    int agg_cpl;            // 8-disparity chunks per lane of the aggregation kernel (1, 2 or 4)
     int schedule;           // SGM_SCHEDULE_PLANES or SGM_SCHEDULE_SWEEP (resolved, never AUTO)
     int sweep_rows;         // rows (warps) per CTA of the fused sweep
     void *sweep_scratch;    // global rings, counters and right map of the fused sweep (null when unsupported)
@@ -118,9 +119,9 @@ int compute_pair(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, uin
 // Drops cached batch graphs that use h (called before h is freed).
 void batch_forget(sgm_handle_s *h);
 // What sgm_autotune chose for h's shape: aggregation blocks per SM (0: not
-// tuned), and the schedule with its rows per CTA.
+// tuned) and chunks per lane, and the schedule with its rows per CTA.
 struct Tuning {
-    int blocks_per_sm, schedule, sweep_rows;
+    int blocks_per_sm, schedule, sweep_rows, cpl;
 };
 Tuning tuned_for(const sgm_handle_s *h);
 // Rows per CTA the fused sweep's scratch is sized for (the smallest it runs with).

@@ -117,15 +117,18 @@ constexpr int kJobClaimBase = 32, kJobClaimSlots = 1024;
 constexpr size_t kJobStateBytes = (size_t)(kJobClaimBase + kJobClaimSlots) * sizeof(unsigned);
 
 // Builds the work list for the directions in `mask` (planes numbered in
-// increasing direction order), longest scanlines first; G = 32 / LPS.
-PathJobs make_path_jobs(int W, int H, int D, int mask);
+// increasing direction order), longest scanlines first, for lanes holding
+// `cpl` 8-disparity chunks each: G = 32 / (lanes_per_scanline(D) / cpl).
+PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl);
+// The most chunks per lane the aggregation takes for D (1 for 16-bit costs, up to 4).
+int chunks_per_lane_max(int D, bool wide);
 
 // One pair of a batched aggregation launch (device-resident table entry).
 struct BatchAggPair {
     const void *cost;  // the pair's cost volume
     void *planes;      // its path planes
     int W, H, D;
-    int lps;           // lanes per scanline for D
+    int lps;           // lanes per scanline: the pixel's chunks / chunks per lane
     int ragged;        // D < 8 * lps
     int nplanes;
     PathJobs jobs;
@@ -162,16 +165,18 @@ cudaError_t launch_sad_cost(const uint8_t *left, const uint8_t *right, int pitch
 // Planes are pixel-interleaved: [H][W][nplanes][Dp], entry k of `jobs` writing
 // plane jobs.plane[k].  job_counter (kJobStateBytes) must have been cleared by
 // the cost kernel launched before it on s.
-// wide: 16-bit costs and planes (SAD), else 8-bit.
+// wide: 16-bit costs and planes (SAD), else 8-bit.  cpl: 8-disparity chunks
+// per lane (1, 2 or 4, at most chunks_per_lane_max; jobs built with the same).
 cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, int P2, bool wide,
                              const PathJobs &jobs, uint8_t *planes, int nplanes,
-                             unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
+                             unsigned *job_counter, int blocks_per_sm, int cpl, cudaStream_t s);
 // All pairs' aggregation in one persistent launch (pairs: device table of
 // npairs entries; prefix: device [2][npairs + 1], the running counts of the
 // pairs' long-axis jobs and of their other jobs).  job_counter as above, for
 // this launch alone.  P1/P2 and the cost width are shared by the pairs.
+// cpl: 1 or 4 (4 only for 8-bit costs and pairs whose D allows it).
 cudaError_t launch_aggregate_batch(const BatchAggPair *pairs, int npairs, const int *prefix, int P1, int P2,
-                                   bool wide, unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
+                                   bool wide, int cpl, unsigned *job_counter, int blocks_per_sm, cudaStream_t s);
 // Copies a single plane ([H][W][Dp], lane-chunk order) to L ([H][W][D] uint16, natural order).
 cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,
                              cudaStream_t s);

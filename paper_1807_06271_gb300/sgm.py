@@ -111,12 +111,14 @@ _SIGNATURES = {
     "sgm_scratch_bytes": [_I, _I, _I, ctypes.POINTER(_Params), _P, _P, _P],
     "sgm_probe_int_rate": [_I, _I, _P, _P],
     "sgm_set_schedule": [_P, _I, _I],
+    "sgm_set_aggregation": [_P, _I, _I],
+    "sgm_get_aggregation": [_P, _P, _P],
     "sgm_batch_create": [_I, _P, _P, _P, ctypes.POINTER(_Params), ctypes.POINTER(_P)],
     "sgm_batch_destroy": [_P],
     "sgm_batch_run": [_P, _P, _P, _P, _P, _P, _P],
-    "sgm_batch_set_tuning": [_P, _I, _I],
-    "sgm_batch_get_tuning": [_P, _P, _P],
-    "sgm_batch_autotune": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "sgm_batch_set_tuning": [_P, _I, _I, _I],
+    "sgm_batch_get_tuning": [_P, _P, _P, _P],
+    "sgm_batch_autotune": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "sgm_batch_device_bytes": [_P, _P],
     "sgm_get_schedule": [_P, _P, _P],
 }
@@ -409,19 +411,22 @@ class Batch:
         _check(load().sgm_batch_run(self._b, *self._arrays(left, right, disp, umap, vmap), _stream(stream)),
                "sgm_batch_run")
 
-    def set_tuning(self, groups: int, blocks_per_sm: int):
-        _check(load().sgm_batch_set_tuning(self._b, groups, blocks_per_sm), "sgm_batch_set_tuning")
+    def set_tuning(self, groups: int, blocks_per_sm: int, chunks_per_lane: int = 1):
+        _check(load().sgm_batch_set_tuning(self._b, groups, blocks_per_sm, chunks_per_lane), "sgm_batch_set_tuning")
 
     def tuning(self):
-        g, b = _I(), _I()
-        _check(load().sgm_batch_get_tuning(self._b, ctypes.byref(g), ctypes.byref(b)), "sgm_batch_get_tuning")
-        return g.value, b.value
+        """(groups, blocks_per_sm, chunks_per_lane)"""
+        g, b, c = _I(), _I(), _I()
+        _check(load().sgm_batch_get_tuning(self._b, ctypes.byref(g), ctypes.byref(b), ctypes.byref(c)),
+               "sgm_batch_get_tuning")
+        return g.value, b.value, c.value
 
     def autotune(self, left, right, disp, umap=None, vmap=None, stream=None):
-        g, b = _I(), _I()
+        """(groups, blocks_per_sm, chunks_per_lane) chosen."""
+        g, b, c = _I(), _I(), _I()
         _check(load().sgm_batch_autotune(self._b, *self._arrays(left, right, disp, umap, vmap), _stream(stream),
-                                         ctypes.byref(g), ctypes.byref(b)), "sgm_batch_autotune")
-        return g.value, b.value
+                                         ctypes.byref(g), ctypes.byref(b), ctypes.byref(c)), "sgm_batch_autotune")
+        return g.value, b.value, c.value
 
     def device_bytes(self) -> int:
         v = ctypes.c_size_t()
@@ -441,8 +446,8 @@ def sgm_batch_run(b: Batch, left, right, disp, umap=None, vmap=None, stream=None
     b.run(left, right, disp, umap, vmap, stream)
 
 
-def sgm_batch_set_tuning(b: Batch, groups: int, blocks_per_sm: int):
-    b.set_tuning(groups, blocks_per_sm)
+def sgm_batch_set_tuning(b: Batch, groups: int, blocks_per_sm: int, chunks_per_lane: int = 1):
+    b.set_tuning(groups, blocks_per_sm, chunks_per_lane)
 
 
 def sgm_batch_get_tuning(b: Batch):
@@ -455,6 +460,18 @@ def sgm_batch_autotune(b: Batch, left, right, disp, umap=None, vmap=None, stream
 
 def sgm_batch_device_bytes(b: Batch) -> int:
     return b.device_bytes()
+
+
+def sgm_set_aggregation(h: Handle, blocks_per_sm: int, chunks_per_lane: int):
+    """Aggregation kernel shape of later calls on h (see sgm.h)."""
+    _check(load().sgm_set_aggregation(h.ptr, blocks_per_sm, chunks_per_lane), "sgm_set_aggregation")
+
+
+def sgm_get_aggregation(h: Handle):
+    """(blocks_per_sm, chunks_per_lane) in use on h."""
+    a, b = _I(), _I()
+    _check(load().sgm_get_aggregation(h.ptr, ctypes.byref(a), ctypes.byref(b)), "sgm_get_aggregation")
+    return a.value, b.value
 
 
 def sgm_set_schedule(h: Handle, schedule: int, rows_per_cta: int = 4):

@@ -180,13 +180,13 @@ class Engine:
                 assert np.array_equal(u16(self.U[i]), u) and np.array_equal(u16(self.V[i]), v), i
 
 
-@pytest.mark.parametrize("groups,bps", [(1, 3), (2, 2), (4, 4), (8, 1)])
-def test_engine_matches_single_pairs_at_each_tuning(groups, bps):
-    specs = [(160, 96, 64), (97, 61, 128), (64, 40, 32), (300, 20, 16), (20, 200, 48), (257, 33, 128),
-             (45, 45, 100), (128, 64, 255), (1, 9, 8)]
+@pytest.mark.parametrize("groups,bps,cpl", [(1, 3, 1), (2, 2, 1), (4, 4, 1), (8, 1, 1), (1, 2, 4), (4, 3, 4)])
+def test_engine_matches_single_pairs_at_each_tuning(groups, bps, cpl):
+    specs = [(160, 96, 64), (97, 61, 128), (64, 40, 32), (300, 20, 40), (20, 200, 48), (257, 33, 128),
+             (45, 45, 100), (128, 64, 255), (1, 9, 33)]
     e = Engine(specs, seed0=500 + groups)
-    e.b.set_tuning(groups, bps)
-    assert e.b.tuning() == (min(groups, len(specs)), bps)
+    e.b.set_tuning(groups, bps, cpl)
+    assert e.b.tuning() == (min(groups, len(specs)), bps, cpl)
     e.run()
     e.check_all()
     for i in (0, 2, 6):  # and the oracle, on a few
@@ -237,8 +237,8 @@ def test_engine_64_mixed_pairs_autotuned():
     di = rng.integers(0, 1, 64)
     specs = [(sizes[a][0], sizes[a][1], (64, 128)[b]) for a, b in zip(si, di)]
     e = Engine(specs, seed0=1807 + 3)
-    g, bps = e.b.autotune(e.L, e.R, e.Dd, e.U, e.V)
-    assert g in (1, 2, 4, 8, 16, 32, 64) and bps in (2, 3, 4)
+    g, bps, cpl = e.b.autotune(e.L, e.R, e.Dd, e.U, e.V)
+    assert g in (1, 2, 4, 8, 16, 32, 64) and bps in (2, 3, 4) and cpl in (1, 4)
     e.run()
     e.check_all()
     # each handle would also hold its own work-queue state (4228 bytes); the

@@ -479,6 +479,13 @@ def kernel_rooflines(w, stage, peaks, hbm_gbs):
             a = pc * de / t / 1e12
             out["cost"] = {"bound": "popc", "popc_per_de": pc, "achieved_tpopc": a, "frac": a / peaks["popc_tops"],
                            "us": t * 1e6}
+    t = mean_s("sweep")
+    if t:
+        # the fused sweep does the cost, every path, the sums and both winners
+        ops = path_ops(w)
+        a = ops * de / t / 1e12
+        out["sweep"] = {"bound": "alu", "ops_per_de": ops, "achieved_tops": a, "frac": a / peaks["int32_tops"],
+                        "us": t * 1e6}
     t = mean_s("wta_lr")
     if t:
         byts = w.W * w.H * (npaths * Dp * eb + 1)
@@ -539,6 +546,13 @@ def run_ours(args, w, windex):
     hbm_gbs, hbm_of = measured_hbm_gbs()
     fp = FramePair(sgm, torch, w, rank_seed(windex, rank), autotune=not args.no_autotune)
     h, left, right, disp, umap, vmap = fp.h, fp.left, fp.right, fp.disp, fp.umap, fp.vmap
+    # optional overrides of what the tuner chose (for profiling one kernel)
+    if args.schedule != "auto":
+        sgm.sgm_set_schedule(h, {"planes": sgm.SGM_SCHEDULE_PLANES, "sweep": sgm.SGM_SCHEDULE_SWEEP}[args.schedule],
+                             args.sweep_rows)
+    if args.cost_kernel != "auto":
+        sgm.sgm_set_cost_kernel(h, {"cuda_cores": sgm.SGM_COST_KERNEL_CUDA_CORES,
+                                    "tensor_cores": sgm.SGM_COST_KERNEL_TENSOR_CORES}[args.cost_kernel])
     params, scene, bps = fp.params, fp.scene, fp.bps
     for _ in range(args.warmup):
         fp.step(stream)
@@ -568,15 +582,16 @@ def run_ours(args, w, windex):
     # the dominant kernel (the aggregation) against the measured INT32 issue
     # rate, and the whole path against min(integer bound, HBM bound)
     kernels = kernel_rooflines(w, stage, peaks, hbm_gbs)
-    agg = kernels["aggregate"]
-    digest = kernel_source_digest(["paper_1807_06271_gb300/csrc/aggregate.cu",
-                                   "paper_1807_06271_gb300/csrc/sgm_internal.cuh"])
-    traffic = profiled_traffic("aggregate", w.name, digest)
+    dom = "aggregate" if "aggregate" in kernels else "sweep"
+    agg = kernels[dom]
+    src = {"aggregate": "aggregate.cu", "sweep": "sweep.cu"}[dom]
+    digest = kernel_source_digest([f"paper_1807_06271_gb300/csrc/{src}", "paper_1807_06271_gb300/csrc/sgm_internal.cuh"])
+    traffic = profiled_traffic(dom, w.name, digest)
     path = path_roofline(w, value / world, peaks, hbm_gbs)
-    roofline = {"bound": "alu", "kernel": "aggregate", "achieved": agg["achieved_tops"],
+    roofline = {"bound": "alu", "kernel": dom, "achieved": agg["achieved_tops"],
                 "peak": peaks["int32_tops"], "unit": "Tops/s", "frac": agg["frac"], "traffic": traffic,
                 "ops_per_de": agg["ops_per_de"], "of": "measured", "peak_basis": peaks["basis"],
-                "peak_packed": peaks["u16x2_tops"], "frac_packed": agg["frac_packed"],
+                "peak_packed": peaks["u16x2_tops"], "frac_packed": agg.get("frac_packed"),
                 "path_frac": path["frac"], "path": path, "kernels": kernels,
                 "hbm_peak_gbs": hbm_gbs, "hbm_peak_of": hbm_of}
 
@@ -680,8 +695,10 @@ def run_ours(args, w, windex):
                                                                      warmup=3)
         per_config["serve-8cams-30fps-4GB"] = serve_summary(torch, args.line_serve_seconds)
 
-    # census, cost, aggregate, wta_lr, median (a device copy when off), U/V
-    launches_per_step = 4 + (1 if w.median_k > 1 else 0) + (1 if w.uv else 0)
+    # planes: census (or SAD cost), cost, aggregate, wta_lr; sweep: census and
+    # the sweep; then median (a device copy when off) and U/V
+    swept = sgm.sgm_get_schedule(h)[0] == sgm.SGM_SCHEDULE_SWEEP
+    launches_per_step = (2 if swept else (3 if w.cost == 1 else 4)) + (1 if w.median_k > 1 else 0) + (1 if w.uv else 0)
     if rank == 0:
         line = {
             "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": world,
@@ -690,6 +707,8 @@ def run_ours(args, w, windex):
             "data": "synthetic",
             "config": dict(workload_config(w), parallelism=f"replicas{world}",
                            agg_blocks_per_sm=bps if bps is not None else "default",
+                           schedule=["auto", "planes", "sweep"][sgm.sgm_get_schedule(h)[0]],
+                           agg_chunks_per_lane=sgm.sgm_get_aggregation(h)[1],
                            l2="flushed between steps (256 MiB write outside the timed events)"),
             "fps": 1e3 / ms_per_step * world,
             "roofline": roofline,
@@ -927,6 +946,11 @@ def main(argv=None):
                     help="length of the serve run inside the default frame line's per_config")
     ap.add_argument("--no-per-config", action="store_true",
                     help="time only the headline workload (no per_config block)")
+    ap.add_argument("--schedule", choices=["auto", "planes", "sweep"], default="auto",
+                    help="path schedule of the headline pair (auto: the tuner's choice)")
+    ap.add_argument("--sweep-rows", type=int, default=8, help="rows per thread block with --schedule sweep")
+    ap.add_argument("--cost-kernel", choices=["auto", "cuda_cores", "tensor_cores"], default="auto",
+                    help="Hamming cost kernel of the headline pair")
     ap.add_argument("--reference-seconds", type=float, default=120.0,
                     help="host time the reference arm's warm-up plus timed steps should take")
     args = ap.parse_args(argv)

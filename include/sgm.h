@@ -358,9 +358,14 @@ int sgm_device_status(sgm_handle h);
  * kernel in a mode whose first wait is on an mbarrier that nothing arrives
  * at, so it gives up after 2 ms and records the timeout.  The matrix
  * products still complete and the handle stays usable; the cost volume of
- * this call is not valid.  A following sgm_device_status(h) returns
- * SGM_ERR_TIMEOUT.  SGM_ERR_UNSUPPORTED where the tensor-core kernel cannot
- * serve the handle (see sgm_debug_cost). */
+ * this call is not valid.  On a handle using SGM_SCHEDULE_SWEEP it runs the
+ * census and the fused sweep with row 1 waiting for a pixel the row above
+ * never publishes: that wait gives up after 2 ms, every other row's wait
+ * then ends at once, and this call's disparity map is not valid.  A
+ * following sgm_device_status(h) returns SGM_ERR_TIMEOUT.
+ * SGM_ERR_UNSUPPORTED where the tensor-core kernel cannot serve the handle
+ * (see sgm_debug_cost), or, for the sweep, when the image has one row, the
+ * sweep runs one row per block, or no enabled path comes from the row above. */
 int sgm_debug_stalled_wait(sgm_handle h, const uint8_t *left, const uint8_t *right, void *stream);
 
 /* ---- fault-detection hooks (tests) ---------------------------------------- */

@@ -670,6 +670,20 @@ int sgm_debug_cost(sgm_handle h, const uint8_t *left, const uint8_t *right, int 
 
 int sgm_debug_stalled_wait(sgm_handle h, const uint8_t *left, const uint8_t *right, void *stream) {
     if (!h || !left || !right) return SGM_ERR_INVALID_ARG;
+    if (h->schedule == SGM_SCHEDULE_SWEEP) {
+        // the fused sweep: row 1 waits for a pixel row 0 never publishes
+        if (h->H < 2 || h->sweep_rows < 2 || !(h->p.path_mask & 0x54)) return SGM_ERR_UNSUPPORTED;
+        DeviceGuard g(h->device);
+        if (!g.ok) return SGM_ERR_CUDA;
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = run_census(h, left, right, s);
+        if (rc == SGM_OK &&
+            launch_sweep(h->codes, h->code_bytes, h->W, h->H, h->D, h->nbits, h->p.P1, h->p.P2, h->p.path_mask,
+                         h->p.lr_tolerance, h->disp_lr, nullptr, nullptr, h->sweep_scratch, h->dev_status,
+                         h->sweep_rows, s, 1) != cudaSuccess)
+            rc = SGM_ERR_CUDA;
+        return rc;
+    }
     int rc = check_cost_kernel(h, SGM_COST_KERNEL_TENSOR_CORES);
     if (rc != SGM_OK) return rc;
     DeviceGuard g(h->device);

@@ -200,8 +200,10 @@ cudaError_t launch_uvmap(const uint8_t *disp, int W, int H, int D, uint16_t *uma
 bool sweep_supported(int D, int mask, int code_bytes);
 bool sweep_fits(int H, int D, int code_bytes, int rows_per_cta);
 size_t sweep_scratch_bytes(int W, int H, int D, int rows_per_cta);
+// stall_test != 0: row 1 waits for a pixel row 0 never publishes, with a 2 ms
+// limit, so that the bounded waits take their timeout path (for tests of it).
 cudaError_t launch_sweep(const void *codes, int code_bytes, int W, int H, int D, int nbits, int P1, int P2,
                          int mask, int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
-                         void *scratch, unsigned *status, int rows_per_cta, cudaStream_t s);
+                         void *scratch, unsigned *status, int rows_per_cta, cudaStream_t s, int stall_test = 0);
 
 }  // namespace sgm

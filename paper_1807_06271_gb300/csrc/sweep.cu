@@ -51,6 +51,7 @@ constexpr int kLandAhead = 8;   // pixels fetched ahead from the global ring
 constexpr int kGSlots = 64;     // slots of a global ring between two CTAs
 constexpr int kPub = 4;         // a global ring's counters move every kPub pixels
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bounded waits: one second
+constexpr unsigned long long kStallTestNs = 2000000ull;  // the stalled-wait test gives up after 2 ms
 
 __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
     uint32_t r;
@@ -140,6 +141,9 @@ struct SweepArgs {
     uint32_t *gprog;        // [2 * (nctas + 1)]: producer progress, consumer progress per boundary,
                             // then the grid's abort word (all zeroed before the launch)
     uint32_t *status;       // device status word (SGM_ERR_TIMEOUT record), may be null
+    unsigned long long wait_ns;  // how long a wait may take before it gives up
+    int stall_row;          // test of the bounded waits: this row waits for a pixel
+                            // the row above never publishes (-1: none)
 };
 
 constexpr int kSweepH = 1, kSweepV = 2, kSweepDL = 4, kSweepDR = 8;
@@ -225,6 +229,7 @@ __device__ __forceinline__ CodeT shfl_up_code(CodeT v) {
 struct Abort {
     uint32_t *word;    // zeroed before the launch
     uint32_t *status;  // the handle's status word, may be null
+    unsigned long long limit_ns;
     __device__ __forceinline__ bool raised() const { return *(volatile const uint32_t *)word != 0u; }
     __device__ __forceinline__ void raise() const {
         atomicExch(word, 1u);
@@ -241,7 +246,7 @@ __device__ __forceinline__ bool wait_cta(const uint32_t *p, uint32_t need, const
         for (;;) {
             ok = ld_acquire_cta(p) >= need;
             if (__all_sync(kFull, ok)) break;
-            if (ab.raised() || now_ns() - t0 > kWaitNs) {
+            if (ab.raised() || now_ns() - t0 > ab.limit_ns) {
                 ok = false;
                 break;
             }
@@ -265,7 +270,7 @@ __device__ __forceinline__ bool wait_gpu(const uint32_t *p, uint32_t need, const
                 ok = true;
                 break;
             }
-            if (ab.raised() || now_ns() - t0 > kWaitNs) break;
+            if (ab.raised() || now_ns() - t0 > ab.limit_ns) break;
         }
     }
     ok = __all_sync(kFull, ok);
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     GRing *gout = reinterpret_cast<GRing *>(a.grings) + blockIdx.x + 1;   // boundary (blockIdx -> blockIdx+1)
     uint32_t *gprod_in = a.gprog + blockIdx.x, *gcons_in = a.gprog + nb + blockIdx.x;
     uint32_t *gprod_out = a.gprog + blockIdx.x + 1, *gcons_out = a.gprog + nb + blockIdx.x + 1;
-    const Abort ab{a.gprog + 2 * nb, a.status};
+    const Abort ab{a.gprog + 2 * nb, a.status, a.wait_ns};
     LRing *rin = warp > 0 ? rings + (warp - 1) : nullptr;
     LRing *rout = (has_cons && !cons_global) ? rings + warp : nullptr;
     uint32_t *my_prog = prog + warp;
@@ -401,7 +406,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
                 // consumption, for the producer's back-pressure
                 if (lane == 0 && ((x + 1) % kPub == 0 || x + 1 == W)) st_release_gpu(gcons_in, (uint32_t)(x + 1));
             } else {
-                ok = wait_cta(in_prog, (uint32_t)min(x + lag, W), ab);
+                // (the stalled-wait test asks for a pixel past the row's end)
+                ok = wait_cta(in_prog, y == a.stall_row ? (uint32_t)W + 1u : (uint32_t)min(x + lag, W), ab);
                 if (!ok) break;
                 const int ls = x % kSlots;
                 wv = ring_words<N>(rin, ls, 0, lane);
@@ -670,8 +676,10 @@ size_t sweep_scratch_bytes(int W, int H, int D, int rows_per_cta) {
 
 cudaError_t launch_sweep(const void *codes, int code_bytes, int W, int H, int D, int nbits, int P1, int P2,
                          int mask, int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,
-                         void *scratch, unsigned *status, int rows_per_cta, cudaStream_t s) {
+                         void *scratch, unsigned *status, int rows_per_cta, cudaStream_t s, int stall_test) {
     if (!sweep_supported(D, mask, code_bytes) || rows_per_cta < 1 || rows_per_cta > 8) return cudaErrorInvalidValue;
+    // the stalled row must have a producer inside its block (row 1, same block as row 0)
+    if (stall_test && (H < 2 || rows_per_cta < 2 || !(mask & 0x54))) return cudaErrorInvalidValue;
     const int R = rows_per_cta;
     const int nctas = (H + R - 1) / R;
     const int DPL = D <= 64 ? 2 : 4;
@@ -695,6 +703,8 @@ cudaError_t launch_sweep(const void *codes, int code_bytes, int W, int H, int D,
     a.dr_map = dbg_right ? dbg_right : reinterpret_cast<uint8_t *>(a.gprog) + counter_bytes(nctas);
     a.dbg_left = dbg_left;
     a.status = status;
+    a.wait_ns = stall_test ? kStallTestNs : kWaitNs;
+    a.stall_row = stall_test ? 1 : -1;
     cudaError_t e = cudaMemsetAsync(a.gprog, 0, counter_bytes(nctas), s);
     if (e != cudaSuccess) return e;
     const bool rag = D != 32 * DPL;

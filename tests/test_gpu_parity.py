@@ -572,3 +572,56 @@ def test_every_tuner_setting_is_bit_exact(name, bps, monkeypatch):
         assert sgm.sgm_device_status(h) == sgm.SGM_OK
         assert_same(u16(S), o["S"], f"S at {bps} blocks/SM")
         assert_same(disp.cpu().numpy(), o["disp"], f"disp at {bps} blocks/SM")
+
+
+# W, H, D, window, mask, P1, P2, LR tol, median
+CPL_CASES = [
+    (150, 70, 128, (9, 7), sgm.SGM_PATHS_8, 8, 96, 1, 3),    # 4 lanes of 4 chunks per scanline
+    (131, 57, 100, (9, 7), sgm.SGM_PATHS_8, 8, 96, 1, 3),    # ragged: padding inside the last lane's chunks
+    (97, 45, 64, (5, 5), sgm.SGM_PATHS_4, 4, 24, 1, 5),      # 2 lanes per scanline
+    (60, 80, 33, (5, 5), sgm.SGM_PATHS_STREAM4, 8, 32, 0, 0),  # one 4-chunk lane per scanline, ragged
+    (40, 30, 255, (3, 3), sgm.SGM_PATHS_8, 2, 10, 1, 3),     # 32 chunks: 8 lanes of 4
+]
+
+
+@pytest.mark.parametrize("cpl", [1, 2, 4])
+@pytest.mark.parametrize("case", CPL_CASES, ids=[f"{c[0]}x{c[1]}d{c[2]}" for c in CPL_CASES])
+def test_every_chunks_per_lane_setting_is_bit_exact(case, cpl):
+    """Each path's L_r, S and the disparity map equal the oracle's with 1, 2
+    and 4 chunks of 8 disparities per lane (sgm_set_aggregation)."""
+    W, H, D, (cw, ch), mask, P1, P2, tol, k = case
+    s = scenes.boxes_scene(W, H, D, seed=W + 7 * cpl, n_boxes=3, dlo=1, dhi=D - 1)
+    o = oracle.sgm(s.left, s.right, D, cw, ch, mask, P1, P2, tol, k, stages=True, uv=False)
+    with sgm.Handle(W, H, D, params(cw, ch, mask, P1, P2, tol, k)) as h:
+        sgm.sgm_set_aggregation(h, 3, cpl)
+        assert sgm.sgm_get_aggregation(h) == (3, cpl)
+        L, R = cuda(s.left), cuda(s.right)
+        S = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
+        disp = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        sgm.sgm_debug_sum(h, L, R, S)
+        h.compute(L, R, disp)
+        for r in (0, 3, 4, 7):
+            if (mask >> r) & 1:
+                Lr = torch.empty((H, W, D), dtype=torch.int16, device="cuda")
+                sgm.sgm_debug_path(h, r, L, R, Lr)
+                torch.cuda.synchronize()
+                cv = oracle.cost_volume(o["codes_l"], o["codes_r"], D, oracle.census_bits(cw, ch))
+                assert_same(u16(Lr), oracle.aggregate_path(cv, r, P1, P2), f"L_{r} with {cpl} chunks per lane")
+        torch.cuda.synchronize()
+        assert_same(u16(S), o["S"], f"S with {cpl} chunks per lane")
+        assert_same(disp.cpu().numpy(), o["disp"], f"disp with {cpl} chunks per lane")
+
+
+def test_chunks_per_lane_limits():
+    with sgm.Handle(64, 32, 16, params(5, 5, sgm.SGM_PATHS_8, 8, 32, 1, 3)) as h:   # D = 16: two chunks per pixel
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_set_aggregation(h, 3, 4)
+        assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_set_aggregation(h, 3, 3)
+        assert e.value.status == sgm.SGM_ERR_INVALID_ARG
+        assert sgm.sgm_get_aggregation(h)[1] == 1
+    sad = params(5, 5, sgm.SGM_PATHS_STREAM4, 200, 800, 1, 5, cost=sgm.SGM_COST_SAD)
+    with sgm.Handle(64, 32, 64, sad) as h:   # 16-bit costs: one chunk per lane
+        with pytest.raises(sgm.SgmError):
+            sgm.sgm_set_aggregation(h, 3, 2)

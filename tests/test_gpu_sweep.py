@@ -141,3 +141,25 @@ def test_sweep_is_refused_where_it_does_not_apply():
         with pytest.raises(sgm.SgmError) as e:
             sgm.sgm_set_schedule(h, sgm.SGM_SCHEDULE_SWEEP, 9)
         assert e.value.status == sgm.SGM_ERR_INVALID_ARG
+
+
+def test_sweep_wait_that_runs_out_is_reported_and_the_handle_recovers():
+    """The fused sweep's bounded waits: with row 1 waiting for a pixel that is
+    never published, the wait gives up after 2 ms, every other row stops, the
+    timeout is reported once, and the next frames are bit-exact again."""
+    W, H, D = 160, 48, 60
+    s = scenes.boxes_scene(W, H, D, seed=5, n_boxes=3, dlo=4, dhi=56)
+    p = sgm.SgmParams(census_w=5, census_h=5, path_mask=0x55, P1=8, P2=32, lr_tolerance=1, median_k=5)
+    ref = oracle.sgm(s.left, s.right, D, 5, 5, 0x55, 8, 32, 1, 5, uv=False)
+    with sgm.Handle(W, H, D, p) as h:
+        sgm.sgm_set_schedule(h, sgm.SGM_SCHEDULE_SWEEP, 4)
+        L, R = cuda(s.left), cuda(s.right)
+        sgm.sgm_debug_stalled_wait(h, L, R)
+        assert sgm.sgm_device_status(h) == sgm.SGM_ERR_TIMEOUT
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK  # reported once
+        for _ in range(2):
+            d = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+            h.compute(L, R, d)
+            torch.cuda.synchronize()
+            assert np.array_equal(d.cpu().numpy(), ref["disp"])
+        assert sgm.sgm_device_status(h) == sgm.SGM_OK

@@ -234,13 +234,16 @@ int sgm_batch_device_bytes(sgm_batch b, size_t *bytes);
 
 /* Shape of the aggregation kernel of later calls on h (the paper has no
  * counterpart): resident 4-warp blocks per SM (1..16) and 8-disparity chunks
- * per lane (1, 2 or 4; SGM_ERR_UNSUPPORTED above what D allows: D must span
- * at least that many chunks, and the 16-bit costs of SGM_COST_SAD take 1).
- * With c chunks per lane a scanline's D disparities occupy D / (8 c) lanes
- * (rounded up to a power of two), so a warp walks more scanlines at once and
- * reduces each one's minimum with fewer shuffles.  Results do not depend on
- * either setting.  A new handle starts with 3 blocks per SM and 1 chunk per
- * lane, or with what sgm_autotune chose for its shape. */
+ * per lane: 1, 2 or 4 for every direction, or SGM_AGG_CHUNKS_MIXED (the
+ * long-axis scanlines, rows when W >= H, at 1 and the other directions at 2).
+ * SGM_ERR_UNSUPPORTED above what D allows (D must span at least that many
+ * chunks; the 16-bit costs of SGM_COST_SAD take 1).  With c chunks per lane a
+ * scanline's D disparities occupy D / (8 c) lanes (rounded up to a power of
+ * two), so a warp walks more scanlines at once with fewer instructions per
+ * disparity estimate, but each step of a scanline takes longer.  Results do
+ * not depend on either setting.  A new handle starts with 3 blocks per SM and
+ * 1 chunk per lane, or with what sgm_autotune chose for its shape. */
+#define SGM_AGG_CHUNKS_MIXED 3
 int sgm_set_aggregation(sgm_handle h, int blocks_per_sm, int chunks_per_lane);
 int sgm_get_aggregation(sgm_handle h, int *blocks_per_sm, int *chunks_per_lane);
 
@@ -275,7 +278,8 @@ int sgm_get_schedule(sgm_handle h, int *schedule, int *rows_per_cta);
 /* Autotuner: times the pipeline on this pair (device pointers as for
  * sgm_compute; disp is overwritten) with the PLANES schedule at 1, 2, 3, 4
  * and 6 resident aggregation blocks per SM, each with 1, 2 and 4 chunks per
- * lane where D allows (sgm_set_aggregation), and, where h can run it, the SWEEP
+ * lane and the mixed layout where D allows (sgm_set_aggregation), and, where
+ * h can run it, the SWEEP
  * schedule at 2, 4 and 8 rows per block; keeps the fastest for h and for
  * handles created later in this process with the same W, H, D, path mask,
  * cost, window and P2.  *best_blocks_per_sm (may be NULL) receives the best

@@ -56,9 +56,8 @@
 
 namespace sgm {
 
-PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl) {
+PathJobs make_path_jobs_mixed(int W, int H, int D, int mask, int cpl_long, int cpl_other) {
     PathJobs j = {};
-    const int G = 32 / (lanes_per_scanline(D) / cpl);
     // long axis first, then the short axis, then the diagonals
     const bool wide = W >= H;
     const int order[kMaxPaths] = {wide ? 0 : 2, wide ? 1 : 3, wide ? 2 : 0, wide ? 3 : 1, 4, 5, 6, 7};
@@ -66,6 +65,8 @@ PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl) {
         const int r = order[i];
         if (!((mask >> r) & 1)) continue;
         const int k = j.n++;
+        j.cpl[k] = i < 2 ? cpl_long : cpl_other;
+        const int G = 32 / (lanes_per_scanline(D) / j.cpl[k]);
         j.dx[k] = dir_dx(r);
         j.dy[k] = dir_dy(r);
         j.plane[k] = __builtin_popcount((unsigned)mask & ((1u << r) - 1u));
@@ -75,6 +76,8 @@ PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl) {
     }
     return j;
 }
+
+PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl) { return make_path_jobs_mixed(W, H, D, mask, cpl, cpl); }
 
 namespace {
 
@@ -202,6 +205,12 @@ __device__ __forceinline__ void st_blk(Blk<CPL, WIDE> *p, const Blk<CPL, WIDE> &
                          "r"(v.w[q]), "r"(v.w[q + 1]), "r"(v.w[q + 2]), "r"(v.w[q + 3]), "l"(pol)
                          : "memory");
     }
+}
+
+// Cost blocks loaded PF steps ahead: 16 for 8-byte blocks, 8 for 16- and 32-byte ones.
+template <int CPL, bool WIDE>
+constexpr int prefetch_depth() {
+    return Blk<CPL, WIDE>::kWords == 2 ? 16 : 8;
 }
 
 // Path state of one lane: chunk c holds R[c][k] = (L[d_c+k], L[d_c+k+4]) packed
@@ -410,13 +419,15 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
     }
 }
 
-template <int LPS, int CPL, bool WIDE, bool RAGGED, int PF>
+// CPL: chunks per lane of the jobs; with CPL2 > CPL, the entries whose
+// jobs.cpl is CPL2 run with CPL2 chunks per lane (LPS * CPL / CPL2 lanes per
+// scanline) and the others with CPL (same cost and plane layout either way).
+template <int LPS, int CPL, bool WIDE, bool RAGGED, int PF, int CPL2 = CPL>
 __global__ void __launch_bounds__(kWarps * 32)
     aggregate_kernel(const Blk<CPL, WIDE> *__restrict__ cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                      PathJobs jobs, Blk<CPL, WIDE> *__restrict__ planes, int nplanes,
                      unsigned *__restrict__ job_counter) {
     wait_for_predecessor();
-    constexpr int G = 32 / LPS;
     const int lane = threadIdx.x & 31;
     const int total = jobs.jbegin[jobs.n];
     const uint64_t pol_stream = policy_evict_first();
@@ -429,8 +440,18 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (job >= (unsigned)total) return;
         int k = 0;
         while ((int)job >= jobs.jbegin[k + 1]) k++;
-        run_job<LPS, CPL, WIDE, RAGGED, PF>(cost, planes, W, H, D, nplanes, jobs.dx[k], jobs.dy[k], jobs.plane[k],
-                                            jobs.nlines[k], ((int)job - jobs.jbegin[k]) * G, P1x2, P2x2, pol_stream);
+        if (CPL2 != CPL && jobs.cpl[k] == CPL2) {
+            constexpr int L2 = LPS * CPL / CPL2 > 0 ? LPS * CPL / CPL2 : 1;
+            using B2 = Blk<CPL2, WIDE>;
+            run_job<L2, CPL2, WIDE, RAGGED, prefetch_depth<CPL2, WIDE>()>(
+                reinterpret_cast<const B2 *>(cost), reinterpret_cast<B2 *>(planes), W, H, D, nplanes, jobs.dx[k],
+                jobs.dy[k], jobs.plane[k], jobs.nlines[k], ((int)job - jobs.jbegin[k]) * (32 / L2), P1x2, P2x2,
+                pol_stream);
+        } else {
+            run_job<LPS, CPL, WIDE, RAGGED, PF>(cost, planes, W, H, D, nplanes, jobs.dx[k], jobs.dy[k], jobs.plane[k],
+                                                jobs.nlines[k], ((int)job - jobs.jbegin[k]) * (32 / LPS), P1x2,
+                                                P2x2, pol_stream);
+        }
     }
 }
 
@@ -495,12 +516,6 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 }
 
-// Cost blocks loaded PF steps ahead: 16 for 8-byte blocks, 8 for 16- and 32-byte ones.
-template <int CPL, bool WIDE>
-constexpr int prefetch_depth() {
-    return Blk<CPL, WIDE>::kWords == 2 ? 16 : 8;
-}
-
 template <int LPS, int CPL, bool WIDE>
 cudaError_t launch_lps(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2,
                        const PathJobs &jobs, uint8_t *planes, int nplanes, unsigned *job_counter,
@@ -551,6 +566,28 @@ __global__ void unpermute_kernel(const uint8_t *__restrict__ plane, int npx, int
 
 }  // namespace
 
+// Rows (long-axis scanlines) at one chunk per lane, the other directions at two.
+cudaError_t launch_mixed(const uint8_t *cost, int W, int H, int D, uint32_t P1x2, uint32_t P2x2, const PathJobs &jobs,
+                         uint8_t *planes, int nplanes, unsigned *job_counter, int blocks, cudaStream_t s) {
+    using BT = Blk<1, false>;
+    const BT *c = reinterpret_cast<const BT *>(cost);
+    BT *p = reinterpret_cast<BT *>(planes);
+    const int L = lanes_per_scanline(D);
+    const bool rag = D != 8 * L;
+#define SGM_MIX(LL)                                                                                              \
+    return launch_k(rag ? aggregate_kernel<LL, 1, false, true, 16, 2> : aggregate_kernel<LL, 1, false, false, 16, 2>, \
+                    dim3(blocks), dim3(kWarps * 32), 0, s, c, W, H, D, P1x2, P2x2, jobs, p, nplanes, job_counter)
+    switch (L) {
+        case 2: SGM_MIX(2);
+        case 4: SGM_MIX(4);
+        case 8: SGM_MIX(8);
+        case 16: SGM_MIX(16);
+        case 32: SGM_MIX(32);
+        default: return cudaErrorInvalidValue;
+    }
+#undef SGM_MIX
+}
+
 int chunks_per_lane_max(int D, bool wide) {
     const int chunks = lanes_per_scanline(D);  // 8-disparity chunks per pixel
     return wide ? 1 : (chunks >= 4 ? 4 : chunks);
@@ -561,8 +598,8 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
                              unsigned *job_counter, int blocks_per_sm, int cpl, cudaStream_t s) {
     if (jobs.jbegin[jobs.n] == 0) return cudaSuccess;
     if (disparities_per_lane(D) != 8) return cudaErrorInvalidValue;
-    if (cpl != 1 && cpl != 2 && cpl != 4) return cudaErrorInvalidValue;
-    if (cpl > chunks_per_lane_max(D, wide)) return cudaErrorInvalidValue;
+    if (cpl != 1 && cpl != 2 && cpl != 4 && cpl != kMixedCpl) return cudaErrorInvalidValue;
+    if ((cpl == kMixedCpl ? 2 : cpl) > chunks_per_lane_max(D, wide)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -570,6 +607,7 @@ cudaError_t launch_aggregate(const uint8_t *cost, int W, int H, int D, int P1, i
     const int blocks = sms * (blocks_per_sm > 0 ? blocks_per_sm : 2);
     const uint32_t P1x2 = (uint32_t)P1 * 0x00010001u, P2x2 = (uint32_t)P2 * 0x00010001u;
     if (wide) return launch_cpl<1, true>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
+    if (cpl == kMixedCpl) return launch_mixed(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
     if (cpl == 4) return launch_cpl<4, false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
     if (cpl == 2) return launch_cpl<2, false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);
     return launch_cpl<1, false>(cost, W, H, D, P1x2, P2x2, jobs, planes, nplanes, job_counter, blocks, s);

@@ -193,8 +193,8 @@ extern "C" int sgm_autotune(sgm_handle h, const uint8_t *left, const uint8_t *ri
     };
     std::vector<Cand> cands;
     const int cmax = sgm::chunks_per_lane_max(h->D, h->wide != 0);
-    for (int cpl : {1, 2, 4})
-        if (cpl <= cmax)
+    for (int cpl : {1, 2, sgm::kMixedCpl, 4})
+        if ((cpl == sgm::kMixedCpl ? 2 : cpl) <= cmax)
             for (int c : {1, 2, 3, 4, 6}) cands.push_back({SGM_SCHEDULE_PLANES, c, cpl});
     for (int r : {2, 4, 8})
         if (sgm::sweep_feasible(h, r) == SGM_OK) cands.push_back({SGM_SCHEDULE_SWEEP, r, saved_cpl});

@@ -142,7 +142,9 @@ int run_matching(sgm_handle_s *h, const uint8_t *left, const uint8_t *right, cud
 
 // All enabled directions into h->planes, or direction only_r alone into plane 0.
 int run_aggregate(sgm_handle_s *h, int only_r, cudaStream_t s) {
-    const PathJobs jobs = make_path_jobs(h->W, h->H, h->D, only_r >= 0 ? (1 << only_r) : h->p.path_mask, h->agg_cpl);
+    const int mask = only_r >= 0 ? (1 << only_r) : h->p.path_mask;
+    const PathJobs jobs = h->agg_cpl == kMixedCpl ? make_path_jobs_mixed(h->W, h->H, h->D, mask, 1, 2)
+                                                  : make_path_jobs(h->W, h->H, h->D, mask, h->agg_cpl);
     TimingRecord *t = stage_begin(h, kStageAggregate, s);
     cudaError_t e = launch_aggregate(h->cost, h->W, h->H, h->D, h->p.P1, h->p.P2, h->wide != 0, jobs, h->planes,
                                      only_r >= 0 ? 1 : h->npaths, h->job_counter, h->agg_blocks_per_sm, h->agg_cpl, s);
@@ -773,8 +775,10 @@ int sgm_set_schedule(sgm_handle h, int schedule, int rows_per_cta) {
 
 int sgm_set_aggregation(sgm_handle h, int blocks_per_sm, int chunks_per_lane) {
     if (!h || blocks_per_sm < 1 || blocks_per_sm > 16) return SGM_ERR_INVALID_ARG;
-    if (chunks_per_lane != 1 && chunks_per_lane != 2 && chunks_per_lane != 4) return SGM_ERR_INVALID_ARG;
-    if (chunks_per_lane > chunks_per_lane_max(h->D, h->wide != 0)) return SGM_ERR_UNSUPPORTED;
+    if (chunks_per_lane != 1 && chunks_per_lane != 2 && chunks_per_lane != 4 && chunks_per_lane != kMixedCpl)
+        return SGM_ERR_INVALID_ARG;
+    if ((chunks_per_lane == kMixedCpl ? 2 : chunks_per_lane) > chunks_per_lane_max(h->D, h->wide != 0))
+        return SGM_ERR_UNSUPPORTED;
     h->agg_blocks_per_sm = blocks_per_sm;
     h->agg_cpl = chunks_per_lane;
     batch_forget(h);  // captured graphs hold the previous launch shape

@@ -106,6 +106,7 @@ struct PathJobs {
     int dx[kMaxPaths], dy[kMaxPaths];
     int plane[kMaxPaths];      // output plane of entry k
     int nlines[kMaxPaths];
+    int cpl[kMaxPaths];        // 8-disparity chunks per lane of entry k's jobs
     int jbegin[kMaxPaths + 1];
     int nlong;                 // jobs [0, nlong) belong to the long-axis directions
 };
@@ -120,8 +121,13 @@ constexpr size_t kJobStateBytes = (size_t)(kJobClaimBase + kJobClaimSlots) * siz
 // increasing direction order), longest scanlines first, for lanes holding
 // `cpl` 8-disparity chunks each: G = 32 / (lanes_per_scanline(D) / cpl).
 PathJobs make_path_jobs(int W, int H, int D, int mask, int cpl);
+// The same with the long-axis directions (rows when W >= H) at cpl_long chunks
+// per lane and the others at cpl_other.
+PathJobs make_path_jobs_mixed(int W, int H, int D, int mask, int cpl_long, int cpl_other);
 // The most chunks per lane the aggregation takes for D (1 for 16-bit costs, up to 4).
 int chunks_per_lane_max(int D, bool wide);
+// Chunks-per-lane code of the mixed layout: long-axis scanlines at 1, the others at 2.
+constexpr int kMixedCpl = SGM_AGG_CHUNKS_MIXED;
 
 // One pair of a batched aggregation launch (device-resident table entry).
 struct BatchAggPair {

@@ -39,6 +39,7 @@ STAGES = ("census", "cost", "aggregate", "wta_lr", "median", "uvmap", "sweep")
 SGM_SCHEDULE_AUTO = 0
 SGM_SCHEDULE_PLANES = 1  # independent scanlines over a cost volume, one plane per direction
 SGM_SCHEDULE_SWEEP = 2  # the paper's streaming set in one fused top-down sweep
+SGM_AGG_CHUNKS_MIXED = 3  # sgm_set_aggregation: rows at 1 chunk per lane, other directions at 2
 
 
 class SgmError(RuntimeError):

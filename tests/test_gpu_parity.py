@@ -584,7 +584,7 @@ CPL_CASES = [
 ]
 
 
-@pytest.mark.parametrize("cpl", [1, 2, 4])
+@pytest.mark.parametrize("cpl", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", CPL_CASES, ids=[f"{c[0]}x{c[1]}d{c[2]}" for c in CPL_CASES])
 def test_every_chunks_per_lane_setting_is_bit_exact(case, cpl):
     """Each path's L_r, S and the disparity map equal the oracle's with 1, 2
@@ -618,7 +618,7 @@ def test_chunks_per_lane_limits():
             sgm.sgm_set_aggregation(h, 3, 4)
         assert e.value.status == sgm.SGM_ERR_UNSUPPORTED
         with pytest.raises(sgm.SgmError) as e:
-            sgm.sgm_set_aggregation(h, 3, 3)
+            sgm.sgm_set_aggregation(h, 3, 5)
         assert e.value.status == sgm.SGM_ERR_INVALID_ARG
         assert sgm.sgm_get_aggregation(h)[1] == 1
     sad = params(5, 5, sgm.SGM_PATHS_STREAM4, 200, 800, 1, 5, cost=sgm.SGM_COST_SAD)

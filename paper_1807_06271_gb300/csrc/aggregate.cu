@@ -34,6 +34,21 @@
 // without a special case.  Disparities d >= D (padding) are parked at 0x7FFF
 // so they never win a minimum or act as a neighbour.
 //
+// Pipes.  On GB300 the packed minima, the byte-permutes and the logic
+// operations issue on the ALU pipe at 16 lanes per cycle, and that pipe
+// bounds the kernel (29.6 of the 42.5 warp instructions of a step on the
+// 1242 x 375, D = 128 workload, 8.1 on the FMA pipe).  The adds that need no
+// three inputs are therefore written as multiply-adds by a 1 the compiler
+// cannot see (the job table's unit field), which run on the FMA pipe: the
+// edge markers, m + P2 - P1, the biased inputs of the cross-lane minimum, the
+// even cost bytes (v - odd * 256) and the plane bytes (hi * 256 + lo).  That
+// moved 6 instructions a step (23.6 ALU, 14.0 FMA) and measured 4-6 % faster;
+// moving the three-input adds as well (two multiply-adds each) balanced the
+// pipes (20.1 / 21.4) but ran slower.  Without any memory access the kernel
+// still takes 135 of its 157 us: the step-to-step chain (lane minimum,
+// cross-lane minimum, next update) bounds it, not HBM, and capping registers
+// for more resident warps (5, 6 or 8 blocks per SM) made that chain slower.
+//
 // Measured and rejected on GB300: 16 disparities per lane (15 % fewer
 // instructions, but the fatter long-axis warps lengthen the critical path);
 // taking the next minimum from the previous step's costs, which moves the
@@ -58,6 +73,7 @@ namespace sgm {
 
 PathJobs make_path_jobs_mixed(int W, int H, int D, int mask, int cpl_long, int cpl_other) {
     PathJobs j = {};
+    j.unit = 1u;
     // long axis first, then the short axis, then the diagonals
     const bool wide = W >= H;
     const int order[kMaxPaths] = {wide ? 0 : 2, wide ? 1 : 3, wide ? 2 : 0, wide ? 3 : 1, 4, 5, 6, 7};
@@ -92,6 +108,13 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
 __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
     uint32_t r;
     asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// a * b + c on the FMA pipe.  With b = `one`, a 1 the compiler cannot see
+// (PathJobs::unit), it is an add that stays off the ALU pipe.
+__device__ __forceinline__ uint32_t mad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
     return r;
 }
 
@@ -139,11 +162,11 @@ __device__ __forceinline__ unsigned next_job(unsigned *state, unsigned nlong, un
 // both halves of x.  The halves are folded first ((m, m) = m * 0x10001 is
 // monotonic in m, so it can be reduced as one 32-bit value).  Scanlines of up
 // to 4 lanes reduce with xor-shuffles; wider ones use one full-warp
-// redux.sync per scanline of the warp, fed 0xFFFFFFFF by the other
-// scanlines' lanes (redux.sync with per-scanline masks measured 2.4x slower
-// on GB300).
+// redux.sync per scanline of the warp, fed x + 0x80008000 by the other
+// scanlines' lanes, more than any (m, m) with m <= 0x7FFF (redux.sync with
+// per-scanline masks measured 2.4x slower on GB300).
 template <int LPS>
-__device__ __forceinline__ uint32_t line_min2(uint32_t x, int grp) {
+__device__ __forceinline__ uint32_t line_min2(uint32_t x, int grp, uint32_t one) {
     constexpr int G = 32 / LPS;
     x = vmin2(x, __byte_perm(x, 0u, 0x1032));
     if constexpr (LPS <= 4) {
@@ -153,14 +176,14 @@ __device__ __forceinline__ uint32_t line_min2(uint32_t x, int grp) {
     } else if constexpr (G == 1) {
         return __reduce_min_sync(0xffffffffu, x);
     } else if constexpr (G == 2) {
-        const uint32_t r0 = __reduce_min_sync(0xffffffffu, grp == 0 ? x : 0xFFFFFFFFu);
-        const uint32_t r1 = __reduce_min_sync(0xffffffffu, grp == 1 ? x : 0xFFFFFFFFu);
+        const uint32_t r0 = __reduce_min_sync(0xffffffffu, mad(x, one, grp == 0 ? 0u : 0x80008000u));
+        const uint32_t r1 = __reduce_min_sync(0xffffffffu, mad(x, one, grp == 1 ? 0u : 0x80008000u));
         return grp ? r1 : r0;
     } else {
         uint32_t m = 0;
 #pragma unroll
         for (int g = 0; g < G; g++) {
-            const uint32_t r = __reduce_min_sync(0xffffffffu, grp == g ? x : 0xFFFFFFFFu);
+            const uint32_t r = __reduce_min_sync(0xffffffffu, mad(x, one, grp == g ? 0u : 0x80008000u));
             if (grp == g) m = r;
         }
         return m;
@@ -229,7 +252,7 @@ struct PathState {
 template <int LPS, int CPL, bool WIDE, bool RAGGED>
 __device__ __forceinline__ void path_step(PathState<CPL> &st, const Blk<CPL, WIDE> &b, uint32_t P1x2,
                                           uint32_t QPx2, int grp, uint32_t lo_edge, uint32_t hi_edge,
-                                          const uint32_t (&inv)[CPL][4]) {
+                                          const uint32_t (&inv)[CPL][4], uint32_t one, uint32_t neg256) {
     uint32_t cc[CPL][4];
 #pragma unroll
     for (int c = 0; c < CPL; c++) {
@@ -240,8 +263,8 @@ __device__ __forceinline__ void path_step(PathState<CPL> &st, const Blk<CPL, WID
 #pragma unroll
             for (int w = 0; w < 2; w++) {
                 const uint32_t v = b.w[2 * c + w];
-                cc[c][2 * w] = v & kLo;                         // bytes 0, 2
-                cc[c][2 * w + 1] = __byte_perm(v, 0u, 0x4341);  // bytes 1, 3
+                cc[c][2 * w + 1] = __byte_perm(v, 0u, 0x4341);     // bytes 1, 3
+                cc[c][2 * w] = mad(cc[c][2 * w + 1], neg256, v);  // bytes 0, 2: v - (bytes 1, 3) * 256
             }
         }
     }
@@ -251,10 +274,12 @@ __device__ __forceinline__ void path_step(PathState<CPL> &st, const Blk<CPL, WID
 #pragma unroll
     for (int c = 0; c < CPL; c++) {
         // (L[d_c-1], L[d_c+3]) and (L[d_c+4], L[d_c+8]); the first/last lane of a
-        // scanline ORs in 0x7FFF for the missing neighbour (lo_edge / hi_edge are 0 elsewhere)
-        const uint32_t dm0 = __byte_perm(c == 0 ? prev : st.R[c - 1][3], st.R[c][3], 0x5432) | (c == 0 ? lo_edge : 0u);
-        const uint32_t dpN =
-            __byte_perm(st.R[c][0], c == CPL - 1 ? next : st.R[c + 1][0], 0x5432) | (c == CPL - 1 ? hi_edge : 0u);
+        // scanline adds 0x7FFF to the missing neighbour (lo_edge / hi_edge are 0
+        // elsewhere), which lifts it to >= 0x7FFF without a carry out of its half
+        uint32_t dm0 = __byte_perm(c == 0 ? prev : st.R[c - 1][3], st.R[c][3], 0x5432);
+        if (c == 0) dm0 = mad(lo_edge, one, dm0);
+        uint32_t dpN = __byte_perm(st.R[c][0], c == CPL - 1 ? next : st.R[c + 1][0], 0x5432);
+        if (c == CPL - 1) dpN = mad(hi_edge, one, dpN);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const uint32_t lm = k == 0 ? dm0 : st.R[c][k - 1];
@@ -278,15 +303,16 @@ __device__ __forceinline__ void path_step(PathState<CPL> &st, const Blk<CPL, WID
     for (int c = 0; c < CPL; c++)
 #pragma unroll
         for (int k = 0; k < 4; k++) st.R[c][k] = n[c][k];
-    st.m2 = line_min2<LPS>(mn, grp);
-    st.mQ = st.m2 + QPx2;
+    st.m2 = line_min2<LPS>(mn, grp, one);
+    st.mQ = mad(st.m2, one, QPx2);
 }
 
 // The lane's path costs in the cost volume's order.  Padding slots (0x7FFF)
 // are stored as their low byte (8-bit) or as 0 (16-bit), so that sums over
 // the planes never carry out of a 16-bit half; no WTA key uses them.
 template <int CPL, bool WIDE, bool RAGGED>
-__device__ __forceinline__ Blk<CPL, WIDE> pack_plane(const PathState<CPL> &st, const uint32_t (&inv)[CPL][4]) {
+__device__ __forceinline__ Blk<CPL, WIDE> pack_plane(const PathState<CPL> &st, const uint32_t (&inv)[CPL][4],
+                                                     uint32_t c256) {
     Blk<CPL, WIDE> b;
 #pragma unroll
     for (int c = 0; c < CPL; c++) {
@@ -301,7 +327,7 @@ __device__ __forceinline__ Blk<CPL, WIDE> pack_plane(const PathState<CPL> &st, c
                     lo &= kLo;
                     hi &= kLo;
                 }
-                b.w[2 * c + i] = hi * 256u + lo;
+                b.w[2 * c + i] = mad(hi, c256, lo);
             }
         }
     }
@@ -315,9 +341,10 @@ __device__ __forceinline__ Blk<CPL, WIDE> pack_plane(const PathState<CPL> &st, c
 template <int LPS, int CPL, bool WIDE, bool RAGGED, int PF>
 __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost, Blk<CPL, WIDE> *__restrict__ planes,
                                         int W, int H, int D, int nplanes, int dx, int dy, int plane, int nlines,
-                                        int s0, uint32_t P1x2, uint32_t P2x2, uint64_t pol_stream) {
+                                        int s0, uint32_t P1x2, uint32_t P2x2, uint64_t pol_stream, uint32_t one) {
     using BT = Blk<CPL, WIDE>;
     const int lane = threadIdx.x & 31;
+    const uint32_t neg256 = one * 0xFFFFFF00u, c256 = one * 256u;
     const int grp = lane / LPS, li = lane % LPS;
     const uint32_t lo_edge = li == 0 ? 0x7FFFu : 0u;            // no d = -1
     const uint32_t hi_edge = li == LPS - 1 ? 0x7FFF0000u : 0u;  // no d = Dp
@@ -390,8 +417,8 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
             const BT c = ring[i];
             ring[i] = ld_blk(cost + ci_ld);
             ci_ld += cstep;
-            path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv);
-            st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv), pol_stream);
+            path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv, one, neg256);
+            st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
             oi += ostep;
         }
         rem -= PF;
@@ -402,8 +429,8 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
             const BT c = ring[i];
             if (rem > PF) ring[i] = ld_blk(cost + ci_ld);
             ci_ld += cstep;
-            path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv);
-            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv), pol_stream);
+            path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv, one, neg256);
+            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
             oi += ostep;
             rem--;
         }
@@ -411,8 +438,8 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
 #pragma unroll
     for (int i = 0; i < PF; i++) {  // the last steps < PF
         if (t0 + i < steps) {
-            path_step<LPS, CPL, WIDE, RAGGED>(st, ring[i], P1x2, QPx2, grp, lo_edge, hi_edge, inv);
-            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv), pol_stream);
+            path_step<LPS, CPL, WIDE, RAGGED>(st, ring[i], P1x2, QPx2, grp, lo_edge, hi_edge, inv, one, neg256);
+            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
             oi += ostep;
             rem--;
         }
@@ -446,11 +473,11 @@ __global__ void __launch_bounds__(kWarps * 32)
             run_job<L2, CPL2, WIDE, RAGGED, prefetch_depth<CPL2, WIDE>()>(
                 reinterpret_cast<const B2 *>(cost), reinterpret_cast<B2 *>(planes), W, H, D, nplanes, jobs.dx[k],
                 jobs.dy[k], jobs.plane[k], jobs.nlines[k], ((int)job - jobs.jbegin[k]) * (32 / L2), P1x2, P2x2,
-                pol_stream);
+                pol_stream, jobs.unit);
         } else {
             run_job<LPS, CPL, WIDE, RAGGED, PF>(cost, planes, W, H, D, nplanes, jobs.dx[k], jobs.dy[k], jobs.plane[k],
                                                 jobs.nlines[k], ((int)job - jobs.jbegin[k]) * (32 / LPS), P1x2,
-                                                P2x2, pol_stream);
+                                                P2x2, pol_stream, jobs.unit);
         }
     }
 }
@@ -499,7 +526,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         BT *planes = reinterpret_cast<BT *>(p.planes);
 #define SGM_JOB(L, RG)                                                                                      \
     run_job<L, CPL, WIDE, RG, PF>(cost, planes, p.W, p.H, p.D, p.nplanes, p.jobs.dx[k], p.jobs.dy[k],       \
-                                  p.jobs.plane[k], p.jobs.nlines[k], s0, P1x2, P2x2, pol_stream)
+                                  p.jobs.plane[k], p.jobs.nlines[k], s0, P1x2, P2x2, pol_stream, p.jobs.unit)
 #define SGM_JOB_L(L)              \
     if (p.ragged) SGM_JOB(L, true); \
     else SGM_JOB(L, false)

@@ -109,6 +109,7 @@ struct PathJobs {
     int cpl[kMaxPaths];        // 8-disparity chunks per lane of entry k's jobs
     int jbegin[kMaxPaths + 1];
     int nlong;                 // jobs [0, nlong) belong to the long-axis directions
+    uint32_t unit;             // always 1; see the kernel's multiply-adds
 };
 
 // Work-queue state of the aggregation kernel (cleared before every launch):

@@ -275,7 +275,10 @@ __device__ __forceinline__ void path_step(PathState<CPL> &st, const Blk<CPL, WID
     for (int c = 0; c < CPL; c++) {
         // (L[d_c-1], L[d_c+3]) and (L[d_c+4], L[d_c+8]); the first/last lane of a
         // scanline adds 0x7FFF to the missing neighbour (lo_edge / hi_edge are 0
-        // elsewhere), which lifts it to >= 0x7FFF without a carry out of its half
+        // elsewhere), which lifts it to >= 0x7FFF without a carry out of its
+        // half.  That needs every lane's values <= 0x7FFF, the neighbour lane's
+        // too when its scanline does not exist or has ended: such lanes run on
+        // zeroed or real cost blocks (run_job), never on uninitialised memory.
         uint32_t dm0 = __byte_perm(c == 0 ? prev : st.R[c - 1][3], st.R[c][3], 0x5432);
         if (c == 0) dm0 = mad(lo_edge, one, dm0);
         uint32_t dpN = __byte_perm(st.R[c][0], c == CPL - 1 ? next : st.R[c + 1][0], 0x5432);
@@ -392,7 +395,7 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
     for (int i = 0; i < PF; i++) {
         if (i < len) {
             ring[i] = ld_blk(cost + ci_ld);
-        } else {
+        } else {  // zeros, so that lanes without a scanline keep bounded values
 #pragma unroll
             for (int q = 0; q < BT::kWords; q++) ring[i].w[q] = 0u;
         }

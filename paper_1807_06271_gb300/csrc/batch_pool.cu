@@ -10,7 +10,11 @@
 //     long-axis scanlines of all its pairs first;
 //   per pair, on its own branch: WTA + right WTA + LR check, median, U/V.
 // With more than one group the groups' branches run side by side, so one
-// group's HBM-bound WTA passes overlap another group's aggregation.  The
+// group's HBM-bound WTA passes overlap another group's aggregation.  A group
+// of one pair runs the single-pair chain instead (its own aggregation kernel
+// on the pair's stream, the work-queue state cleared by the cost kernel), so
+// that with one group per pair the engine does what a graph of handles does,
+// from the pool.  The
 // tuner (sgm_batch_autotune) picks the number of groups (up to one per pair,
 // which is one aggregation launch per pair) and the aggregation kernel's
 // resident blocks per SM.
@@ -166,47 +170,73 @@ int enqueue(sgm_batch_s *b, const uint8_t *const *left, const uint8_t *const *ri
             uint16_t *const *umap, uint16_t *const *vmap, cudaStream_t s) {
     if (cudaEventRecord(b->origin, s) != cudaSuccess) return SGM_ERR_CUDA;
     const RectMaps no_maps{nullptr, nullptr, nullptr, nullptr};
+    // census and matching cost of pair i on its own stream; a non-null
+    // job_state is cleared by the cost kernel
+    auto costs = [&](int i, unsigned *job_state) -> cudaError_t {
+        PairSlot &ps = b->pairs[i];
+        if (cudaStreamWaitEvent(ps.side, b->origin, 0) != cudaSuccess) return cudaErrorUnknown;
+        if (b->wide)
+            return launch_sad_cost(left[i], right[i], ps.W, ps.W, ps.H, ps.D, b->p.census_w, b->p.census_h, no_maps,
+                                   reinterpret_cast<uint16_t *>(b->pool + ps.cost), job_state, ps.side);
+        cudaError_t e = launch_census(left[i], right[i], ps.W, ps.W, ps.H, b->p.census_w, b->p.census_h,
+                                      b->code_bytes, b->pool + ps.codes, no_maps, ps.side);
+        if (e == cudaSuccess)
+            e = launch_cost(b->pool + ps.codes, b->code_bytes, ps.W, ps.H, ps.D, b->nbits, b->pool + ps.cost,
+                            job_state, nullptr, SGM_COST_KERNEL_AUTO, ps.side);
+        return e;
+    };
+    // WTA + LR check, median and U/V of pair i on its own stream, then join s
+    auto finish = [&](int i) -> int {
+        PairSlot &ps = b->pairs[i];
+        uint8_t *lr = b->pool + ps.disp_lr;
+        cudaError_t e = launch_wta(b->pool + ps.planes, b->npaths, ps.W, ps.H, ps.D, b->wide != 0,
+                                   b->p.lr_tolerance, lr, nullptr, nullptr, nullptr, ps.side);
+        if (e == cudaSuccess)
+            e = b->p.median_k <= 1 ? cudaMemcpyAsync(disp[i], lr, (size_t)ps.W * ps.H, cudaMemcpyDeviceToDevice, ps.side)
+                                   : launch_median(lr, disp[i], ps.W, ps.H, b->p.median_k, ps.side);
+        if (e == cudaSuccess && umap && vmap && umap[i] && vmap[i])
+            e = launch_uvmap(disp[i], ps.W, ps.H, ps.D, umap[i], vmap[i], ps.side);
+        if (e != cudaSuccess || cudaEventRecord(ps.done, ps.side) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ps.done, 0) != cudaSuccess)
+            return SGM_ERR_CUDA;
+        return SGM_OK;
+    };
     for (Group &g : b->groups) {
+        unsigned *job_state = reinterpret_cast<unsigned *>(b->pool + g.job_state);
+        if (g.pairs.size() == 1) {
+            // One pair: the single-pair chain on the pair's stream, with its
+            // own specialised aggregation kernel; the cost kernel clears the
+            // work-queue state, so every launch keeps the programmatic
+            // (overlapped) dependency on the one before it.
+            const int i = g.pairs[0];
+            PairSlot &ps = b->pairs[i];
+            const PathJobs jobs = make_path_jobs(ps.W, ps.H, ps.D, b->p.path_mask, b->cpl);
+            if (costs(i, job_state) != cudaSuccess ||
+                launch_aggregate(b->pool + ps.cost, ps.W, ps.H, ps.D, b->p.P1, b->p.P2, b->wide != 0, jobs,
+                                 b->pool + ps.planes, b->npaths, job_state, b->blocks_per_sm, b->cpl,
+                                 ps.side) != cudaSuccess)
+                return SGM_ERR_CUDA;
+            const int rc = finish(i);
+            if (rc != SGM_OK) return rc;
+            continue;
+        }
         if (cudaStreamWaitEvent(g.stream, b->origin, 0) != cudaSuccess) return SGM_ERR_CUDA;
         for (int i : g.pairs) {
             PairSlot &ps = b->pairs[i];
-            if (cudaStreamWaitEvent(ps.side, b->origin, 0) != cudaSuccess) return SGM_ERR_CUDA;
-            cudaError_t e;
-            if (b->wide) {
-                e = launch_sad_cost(left[i], right[i], ps.W, ps.W, ps.H, ps.D, b->p.census_w, b->p.census_h, no_maps,
-                                    reinterpret_cast<uint16_t *>(b->pool + ps.cost), nullptr, ps.side);
-            } else {
-                e = launch_census(left[i], right[i], ps.W, ps.W, ps.H, b->p.census_w, b->p.census_h, b->code_bytes,
-                                  b->pool + ps.codes, no_maps, ps.side);
-                if (e == cudaSuccess)
-                    e = launch_cost(b->pool + ps.codes, b->code_bytes, ps.W, ps.H, ps.D, b->nbits, b->pool + ps.cost,
-                                    nullptr, nullptr, SGM_COST_KERNEL_AUTO, ps.side);
-            }
-            if (e != cudaSuccess || cudaEventRecord(ps.ready, ps.side) != cudaSuccess ||
+            if (costs(i, nullptr) != cudaSuccess || cudaEventRecord(ps.ready, ps.side) != cudaSuccess ||
                 cudaStreamWaitEvent(g.stream, ps.ready, 0) != cudaSuccess)
                 return SGM_ERR_CUDA;
         }
-        if (cudaMemsetAsync(b->pool + g.job_state, 0, kJobStateBytes, g.stream) != cudaSuccess ||
+        if (cudaMemsetAsync(job_state, 0, kJobStateBytes, g.stream) != cudaSuccess ||
             launch_aggregate_batch(reinterpret_cast<const BatchAggPair *>(b->pool + g.table), (int)g.pairs.size(),
                                    reinterpret_cast<const int *>(b->pool + g.prefix), b->p.P1, b->p.P2, b->wide != 0,
-                                   b->cpl, reinterpret_cast<unsigned *>(b->pool + g.job_state), b->blocks_per_sm,
-                                   g.stream) != cudaSuccess ||
+                                   b->cpl, job_state, b->blocks_per_sm, g.stream) != cudaSuccess ||
             cudaEventRecord(g.aggregated, g.stream) != cudaSuccess)
             return SGM_ERR_CUDA;
         for (int i : g.pairs) {
-            PairSlot &ps = b->pairs[i];
-            uint8_t *lr = b->pool + ps.disp_lr;
-            if (cudaStreamWaitEvent(ps.side, g.aggregated, 0) != cudaSuccess) return SGM_ERR_CUDA;
-            cudaError_t e = launch_wta(b->pool + ps.planes, b->npaths, ps.W, ps.H, ps.D, b->wide != 0,
-                                       b->p.lr_tolerance, lr, nullptr, nullptr, nullptr, ps.side);
-            if (e == cudaSuccess)
-                e = b->p.median_k <= 1 ? cudaMemcpyAsync(disp[i], lr, (size_t)ps.W * ps.H, cudaMemcpyDeviceToDevice, ps.side)
-                                       : launch_median(lr, disp[i], ps.W, ps.H, b->p.median_k, ps.side);
-            if (e == cudaSuccess && umap && vmap && umap[i] && vmap[i])
-                e = launch_uvmap(disp[i], ps.W, ps.H, ps.D, umap[i], vmap[i], ps.side);
-            if (e != cudaSuccess || cudaEventRecord(ps.done, ps.side) != cudaSuccess ||
-                cudaStreamWaitEvent(s, ps.done, 0) != cudaSuccess)
-                return SGM_ERR_CUDA;
+            if (cudaStreamWaitEvent(b->pairs[i].side, g.aggregated, 0) != cudaSuccess) return SGM_ERR_CUDA;
+            const int rc = finish(i);
+            if (rc != SGM_OK) return rc;
         }
     }
     return SGM_OK;

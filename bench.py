@@ -388,6 +388,48 @@ class FramePair:
         self.h.close()
 
 
+def stream_rate(torch, sgm, fp, ns, pairs, stream):
+    """Consecutive pairs spread round-robin over ns handles on ns streams
+    (fp's handle plus ns - 1 new ones of the same shape, which start from the
+    tuner's choice for it): one pair's HBM-bound WTA overlaps other pairs'
+    aggregation, as a stream of frames is best run.  No L2 flush between
+    pairs.  Returns ms per pair."""
+    w = fp.w
+    extra = [sgm.Handle(w.W, w.H, w.D, fp.params) for _ in range(ns - 1)]
+    try:
+        hs = [fp.h] + extra
+        ss = [torch.cuda.Stream() for _ in range(ns)]
+        ds = [fp.disp] + [torch.empty_like(fp.disp) for _ in extra]
+        us = [fp.umap] + [torch.empty_like(fp.umap) for _ in extra]
+        vs = [fp.vmap] + [torch.empty_like(fp.vmap) for _ in extra]
+
+        def one(i):
+            k = i % ns
+            hs[k].compute(fp.left, fp.right, ds[k], ss[k])
+            if w.uv:
+                hs[k].uvmap(ds[k], us[k], vs[k], ss[k])
+
+        for i in range(2 * ns):
+            one(i)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for st in ss:
+            st.wait_event(c0)
+        for i in range(pairs):
+            one(i)
+        for st in ss:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        return c0.elapsed_time(c1) / pairs
+    finally:
+        for h in extra:
+            h.close()
+
+
 def timed_steps(torch, fp, stream, flush, steps):
     """CUDA-event time of each of `steps` steps, L2 flushed before each
     (outside the events)."""
@@ -519,11 +561,14 @@ def per_config_line(torch, sgm, w, windex, steps, stream, flush, peaks, hbm_gbs)
     value = w.de_per_frame / (ms_per_step / 1e3) / 1e6
     stage = stage_pass(sgm, fp, stream, flush, min(steps, 50))
     e2e = e2e_run(torch, sgm, fp, stream, max(3, min(steps, 50)))
+    ms4 = stream_rate(torch, sgm, fp, 4, 200, stream)
     line = {"config": workload_config(w), "value": value, "unit": "MDE/s", "ms_per_step": ms_per_step,
             "fps": 1e3 / ms_per_step, "steps": steps, "e2e": e2e, "agg_blocks_per_sm": fp.bps,
             "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stage.items() if v[1]},
             "kernels": kernel_rooflines(w, stage, peaks, hbm_gbs),
-            "path_roofline": path_roofline(w, value, peaks, hbm_gbs)}
+            "path_roofline": path_roofline(w, value, peaks, hbm_gbs),
+            "four_streams": {"ms_per_pair": ms4, "value": w.de_per_frame / (ms4 / 1e3) / 1e6, "unit": "MDE/s",
+                             "pairs": 200}}
     fp.close()
     return line
 
@@ -595,46 +640,17 @@ def run_ours(args, w, windex):
                 "path_frac": path["frac"], "path": path, "kernels": kernels,
                 "hbm_peak_gbs": hbm_gbs, "hbm_peak_of": hbm_of}
 
-    # Consecutive pairs on two handles and two streams, so that one pair's
-    # HBM-bound WTA overlaps the next pair's aggregation (how a stream of
-    # frames is best run; reported beside the one-pair-per-step value, no L2
-    # flush between pairs).
+    # Consecutive pairs on two and on four handles and streams, so that one
+    # pair's HBM-bound WTA overlaps other pairs' aggregation (how a stream of
+    # frames is best run; reported beside the one-pair-per-step value).
     concurrency = None
     if world == 1:
-        h2 = sgm.Handle(w.W, w.H, w.D, params)
-        if bps is not None:
-            sgm.sgm_autotune(h2, left, right, disp, stream)
-        hs2, ss2 = [h, h2], [torch.cuda.Stream(), torch.cuda.Stream()]
-        ds2 = [disp, torch.empty_like(disp)]
-        us2 = [umap, torch.empty_like(umap)]
-        vs2 = [vmap, torch.empty_like(vmap)]
-
-        def step2(i):
-            k = i & 1
-            hs2[k].compute(left, right, ds2[k], ss2[k])
-            if w.uv:
-                hs2[k].uvmap(ds2[k], us2[k], vs2[k], ss2[k])
-
-        for i in range(4):
-            step2(i)
-        torch.cuda.synchronize()
         n2 = max(10, min(args.steps, 200))
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for st in ss2:
-            st.wait_event(c0)
-        for i in range(n2):
-            step2(i)
-        for st in ss2:
-            ev = torch.cuda.Event()
-            ev.record(st)
-            stream.wait_event(ev)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        ms2 = c0.elapsed_time(c1) / n2
+        ms2 = stream_rate(torch, sgm, fp, 2, n2, stream)
+        ms4 = stream_rate(torch, sgm, fp, 4, n2, stream)
         concurrency = {"streams": 2, "pairs": n2, "ms_per_pair": ms2,
-                       "value": de / (ms2 / 1e3) / 1e6, "unit": "MDE/s"}
-        h2.close()
+                       "value": de / (ms2 / 1e3) / 1e6, "unit": "MDE/s",
+                       "four_streams": {"ms_per_pair": ms4, "value": de / (ms4 / 1e3) / 1e6}}
 
     e2e = e2e_run(torch, sgm, fp, stream, max(3, min(args.steps, 200)), world)
 

@@ -113,8 +113,9 @@ def path_hbm_bytes_per_de(w) -> float:
 
 
 def measured_hbm_gbs():
-    """(GB/s, basis): the measured copy bandwidth of the GB300s,
-    else the profiling recipe's fallback."""
+    """(GB/s, basis): the measured copy bandwidth of this GPU type from
+    MEASURED_PEAKS.json beside the repository, else a 6.8 TB/s fallback (one
+    earlier GB300 measurement)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         v = float(json.load(open(path))["hbm_gbs"])

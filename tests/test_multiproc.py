@@ -98,7 +98,7 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 def test_roofline_host_arithmetic():
     """Ops per estimate of the aggregation kernel (7 per path), of the cost
     and of the whole path (72 for the 8-path 9x7 workload, 37 for the 4-path
-    5x5 ones, as the survey counts them), the HBM bytes the path must move,
+    5x5 ones, counted per estimate as the roofline model does), the HBM bytes the path must move,
     and the path roofline as min(integer bound, HBM bound)."""
     import bench
     from paper_1807_06271_gb300 import scenes

@@ -195,8 +195,8 @@ typedef struct sgm_batch_s *sgm_batch;
 /* A batch of n pairs: pair i has W[i] x H[i] images and D[i] disparities.
  * params are checked for every pair as by sgm_create; row_pitch must be 0
  * (dense rows).  Allocates the pool (see sgm_batch_device_bytes) on the
- * current device, one CUDA stream per pair, and starts with 1 group and 3
- * resident aggregation blocks per SM. */
+ * current device, one CUDA stream per pair, and starts with one group per
+ * pair and 3 resident aggregation blocks per SM. */
 int sgm_batch_create(int n, const int *W, const int *H, const int *D, const sgm_params *params,
                      sgm_batch *out);
 
@@ -212,8 +212,11 @@ int sgm_batch_destroy(sgm_batch b);
 int sgm_batch_run(sgm_batch b, const uint8_t *const *left, const uint8_t *const *right,
                   uint8_t *const *disp, uint16_t *const *umap, uint16_t *const *vmap, void *stream);
 
-/* Number of groups (a power of two up to 64, capped at the number of pairs;
- * pairs are dealt to groups largest first), the aggregation kernel's
+/* Number of groups (a power of two up to 64, capped at the number of pairs,
+ * or n: one group per pair; pairs are dealt to groups largest first).  A
+ * group of one pair runs the single-pair chain on the pair's stream (its own
+ * aggregation launch, overlapped with its cost kernel); larger groups share
+ * one persistent aggregation launch.  Then the aggregation kernel's
  * resident blocks per SM (1..16) and its 8-disparity chunks per lane (1, or
  * 4 when every pair's D spans at least 4 chunks and the cost is census; see
  * sgm_set_aggregation) of later runs.  Synchronises the device when the
@@ -221,8 +224,8 @@ int sgm_batch_run(sgm_batch b, const uint8_t *const *left, const uint8_t *const 
 int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm, int chunks_per_lane);
 int sgm_batch_get_tuning(sgm_batch b, int *groups, int *blocks_per_sm, int *chunks_per_lane);
 
-/* Times runs on these buffers with 1, 2, 4, ... groups (up to one per pair)
- * at 2, 3 and 4 blocks per SM, each with 1 and (where allowed) 4 chunks per
+/* Times runs on these buffers with 1, 2, 4, ... groups and one group per
+ * pair at 2, 3 and 4 blocks per SM, each with 1 and (where allowed) 4 chunks per
  * lane, and keeps the fastest; any output may be NULL.  Synchronises. */
 int sgm_batch_autotune(sgm_batch b, const uint8_t *const *left, const uint8_t *const *right,
                        uint8_t *const *disp, uint16_t *const *umap, uint16_t *const *vmap,

@@ -158,6 +158,7 @@ int make_streams(sgm_batch_s *b) {
             return SGM_ERR_CUDA;
     }
     for (Group &g : b->groups) {
+        if (g.pairs.size() == 1) continue;  // runs on its pair's stream
         if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&g.aggregated, cudaEventDisableTiming) != cudaSuccess)
             return SGM_ERR_CUDA;
@@ -302,7 +303,7 @@ int sgm_batch_create(int n, const int *W, const int *H, const int *D, const sgm_
     b->nbits = b->wide ? params->census_w * params->census_h * 255 : params->census_w * params->census_h - 1;
     b->code_bytes = b->wide ? 0 : (b->nbits <= 32 ? 4 : 8);
     b->npaths = __builtin_popcount((unsigned)params->path_mask);
-    b->ngroups = 1;
+    b->ngroups = n;
     b->blocks_per_sm = 3;
     b->cpl = 1;
     b->cpl_max = 4;
@@ -336,10 +337,12 @@ int sgm_batch_create(int n, const int *W, const int *H, const int *D, const sgm_
     }
     b->tables_at = at;
     size_t tables_end = at;
-    for (int g = 1; g <= kMaxGroups; g *= 2) {
+    for (int g = 1;; g *= 2) {  // every allowed grouping: powers of two up to kMaxGroups, and n
+        const int ng = g <= kMaxGroups ? std::min(g, n) : n;
         size_t end = 0;
-        layout_groups(b, std::min(g, n), false, b->tables_at, &end);
+        layout_groups(b, ng, false, b->tables_at, &end);
         tables_end = std::max(tables_end, end);
+        if (g > kMaxGroups) break;
     }
     b->pool_bytes = tables_end;
     void *pool = nullptr;
@@ -351,7 +354,7 @@ int sgm_batch_create(int n, const int *W, const int *H, const int *D, const sgm_
     b->pool = (unsigned char *)pool;
     b->ngroups = 0;
     int rc = cudaEventCreateWithFlags(&b->origin, cudaEventDisableTiming) == cudaSuccess ? SGM_OK : SGM_ERR_CUDA;
-    if (rc == SGM_OK) rc = regroup(b, 1);
+    if (rc == SGM_OK) rc = regroup(b, n);
     if (rc != SGM_OK) {
         cudaGetLastError();
         free_batch(b);
@@ -376,8 +379,8 @@ int sgm_batch_device_bytes(sgm_batch b, size_t *bytes) {
 }
 
 int sgm_batch_set_tuning(sgm_batch b, int groups, int blocks_per_sm, int chunks_per_lane) {
-    if (!b || groups < 1 || groups > kMaxGroups || (groups & (groups - 1)) || blocks_per_sm < 1 || blocks_per_sm > 16)
-        return SGM_ERR_INVALID_ARG;
+    if (!b || groups < 1 || blocks_per_sm < 1 || blocks_per_sm > 16) return SGM_ERR_INVALID_ARG;
+    if (groups != b->n && (groups > kMaxGroups || (groups & (groups - 1)))) return SGM_ERR_INVALID_ARG;
     if (chunks_per_lane != 1 && chunks_per_lane != 4) return SGM_ERR_INVALID_ARG;
     if (chunks_per_lane > b->cpl_max) return SGM_ERR_UNSUPPORTED;
     DeviceSwitch on(b->device);
@@ -470,8 +473,12 @@ int sgm_batch_autotune(sgm_batch b, const uint8_t *const *left, const uint8_t *c
     float best = 1e30f;
     for (int cpl : {1, 4}) {
         if (cpl > b->cpl_max) break;
-        for (int g = 1; g <= kMaxGroups && rc == SGM_OK; g *= 2) {
-            if (g > 1 && (g >> 1) >= b->n) break;  // beyond one group per pair
+        // 1, 2, 4, ... groups below one per pair, then one group per pair
+        std::vector<int> gs;
+        for (int g = 1; g < b->n && g <= kMaxGroups; g *= 2) gs.push_back(g);
+        gs.push_back(b->n);
+        for (int g : gs) {
+            if (rc != SGM_OK) break;
             for (int bps : {2, 3, 4}) {
                 rc = sgm_batch_set_tuning(b, g, bps, cpl);
                 for (int w = 0; w < 2 && rc == SGM_OK; w++) rc = sgm_batch_run(b, left, right, disp, umap, vmap, stream);

@@ -180,7 +180,8 @@ class Engine:
                 assert np.array_equal(u16(self.U[i]), u) and np.array_equal(u16(self.V[i]), v), i
 
 
-@pytest.mark.parametrize("groups,bps,cpl", [(1, 3, 1), (2, 2, 1), (4, 4, 1), (8, 1, 1), (1, 2, 4), (4, 3, 4)])
+@pytest.mark.parametrize("groups,bps,cpl", [(1, 3, 1), (2, 2, 1), (4, 4, 1), (8, 1, 1), (9, 3, 1), (1, 2, 4), (4, 3, 4),
+                                             (9, 2, 4)])
 def test_engine_matches_single_pairs_at_each_tuning(groups, bps, cpl):
     specs = [(160, 96, 64), (97, 61, 128), (64, 40, 32), (300, 20, 40), (20, 200, 48), (257, 33, 128),
              (45, 45, 100), (128, 64, 255), (1, 9, 33)]
@@ -195,6 +196,25 @@ def test_engine_matches_single_pairs_at_each_tuning(groups, bps, cpl):
         o = oracle.sgm(s.left, s.right, D, 9, 7, sgm.SGM_PATHS_8, 8, 96, 1, 3)
         assert np.array_equal(e.Dd[i].cpu().numpy(), o["disp"]), i
         assert np.array_equal(u16(e.U[i]), o["U"]) and np.array_equal(u16(e.V[i]), o["V"]), i
+    e.b.close()
+
+
+def test_engine_groupings_that_are_accepted():
+    """Groups: a power of two up to 64, or exactly one per pair (any count);
+    anything else is refused and leaves the tuning as it was."""
+    specs = [(60, 40, 32), (50, 30, 16), (40, 20, 64)]
+    e = Engine(specs, seed0=40)
+    assert e.b.tuning() == (3, 3, 1)  # starts with one group per pair
+    for g in (1, 2, 4, 3):
+        e.b.set_tuning(g, 2)
+        assert e.b.tuning()[0] == min(g, 3)
+    for bad in (0, 5, 6, 65):
+        with pytest.raises(sgm.SgmError) as err:
+            e.b.set_tuning(bad, 2)
+        assert err.value.status == sgm.SGM_ERR_INVALID_ARG
+    assert e.b.tuning()[0] == 3
+    e.run()
+    e.check_all()
     e.b.close()
 
 
@@ -221,6 +241,10 @@ def test_engine_other_parameter_sets():
                    dict(census_w=5, census_h=5, path_mask=sgm.SGM_PATHS_STREAM4, P1=200, P2=800, lr_tolerance=1,
                         median_k=5, cost=sgm.SGM_COST_SAD)):
         e = Engine(specs, params=params, seed0=20)
+        assert e.b.tuning()[0] == len(specs)  # one group per pair: the single-pair chain
+        e.run()
+        e.check_all()
+        e.b.set_tuning(1, 3)  # all pairs in one persistent aggregation launch
         e.run()
         e.check_all()
         e.b.close()

@@ -163,6 +163,11 @@ class Scheduler:
     def idle(self) -> bool:
         return not self.busy and not self.queue
 
+    def reset_stats(self):
+        """New statistics for the next run, keeping the slots (a warm-up run
+        creates them; the measured run then reuses them)."""
+        self.stats = Stats(max_slots=len(self.slot_key), max_bytes=self.bytes)
+
     def run(self, schedule, clock=time.perf_counter, speed: float = 1.0):
         """Replays (time, stream, index) arrivals against the wall clock
         (``speed`` > 1 compresses time) until every frame has completed."""

@@ -70,6 +70,24 @@ def test_slot_reuse_per_shape_and_no_head_of_line_blocking():
     assert len(sch.queue) == 1
 
 
+def test_warm_up_slots_are_reused_by_the_measured_run():
+    """A warm-up run creates the slots; after reset_stats the measured run
+    reuses them (no slot created while it is timed), counts only its own
+    frames and still reports the slots and bytes held."""
+    spec = serving.StreamSpec("a", 64, 48, 32, fps=1000.0)
+    need = serving.slot_device_bytes(spec)
+    clock = FakeClock()
+    ex = FakeExecutor(clock, service=0.01)
+    sch = serving.Scheduler([spec], ex, memory_budget=2 * need + 1)
+    sch.run([(0.0001 * i, 0, i) for i in range(10)], clock=clock)
+    assert ex.slots == 2
+    sch.reset_stats()
+    st = sch.run([(0.0001 * i, 0, i) for i in range(6)], clock=clock)
+    assert ex.slots == 2  # nothing new allocated
+    assert st.frames == 6 and len(st.latencies_ms) == 6
+    assert st.max_slots == 2 and st.max_bytes == 2 * need
+
+
 def test_poisson_schedule_rates():
     specs = [serving.StreamSpec("a", 8, 8, 8, fps=30.0), serving.StreamSpec("b", 8, 8, 8, fps=60.0)]
     ev = serving.poisson_schedule(specs, duration_s=100.0, seed=7)

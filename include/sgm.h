@@ -375,6 +375,17 @@ int sgm_device_status(sgm_handle h);
  * sweep runs one row per block, or no enabled path comes from the row above. */
 int sgm_debug_stalled_wait(sgm_handle h, const uint8_t *left, const uint8_t *right, void *stream);
 
+/* Guarded builds only (the library compiled with -DSGM_GUARDED, which
+ * paper_1807_06271_gb300.build makes as libsgm_guarded.so for tests; the
+ * paper has no counterpart).  In them the census, CUDA-core cost,
+ * aggregation, WTA, median and U/V kernels check every global index they
+ * compute, and every image-dependent shared-memory index, against the
+ * buffer's extent, skip an access out of range and count it.  Writes to
+ * *hits the count on the current device since the last reset (synchronise
+ * the device first), and resets it when reset != 0.  SGM_ERR_UNSUPPORTED in
+ * the default build; SGM_ERR_CUDA if a counter cannot be read. */
+int sgm_debug_guard_hits(unsigned long long *hits, int reset);
+
 /* ---- fault-detection hooks (tests) ---------------------------------------- */
 
 /* Process-wide: the n-th device allocation the library makes from now on

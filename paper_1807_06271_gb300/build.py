@@ -19,6 +19,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsgm.so")
+# the guarded test variant (-DSGM_GUARDED: index checks in the plane path's kernels)
+GUARDED_BUILD_DIR = os.path.join(PKG, "_build_guarded")
+GUARDED_LIB = os.path.join(PKG, "libsgm_guarded.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -40,22 +43,29 @@ def _deps():
             + [os.path.join(ROOT, "include", "sgm.h"), os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(guarded: bool = False) -> bool:
+    lib = GUARDED_LIB if guarded else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), guarded: bool = False) -> str:
+    """Builds libsgm.so, or with guarded=True the test variant
+    libsgm_guarded.so (-DSGM_GUARDED), each from its own object directory."""
+    lib = GUARDED_LIB if guarded else LIB
+    build_dir = GUARDED_BUILD_DIR if guarded else BUILD_DIR
+    if guarded:
+        extra_flags = (*extra_flags, "-DSGM_GUARDED")
+    if not force and up_to_date(guarded):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, *inc, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,16 +77,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
-    print(build(force="--force" in sys.argv, verbose=v,
+    print(build(force="--force" in sys.argv, verbose=v, guarded="--guarded" in sys.argv,
                 extra_flags=["-Xptxas", "-v"] if v else []))

@@ -390,10 +390,12 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
     const int ostep = cstep * nplanes;
     int ci_ld = pix * LPS + li;  // next cost block to load into the ring
     int oi = (pix * nplanes + plane) * LPS + li;
+    // extents in blocks (guarded builds check every index against them)
+    const long long cost_blocks = (long long)W * H * LPS, plane_blocks = cost_blocks * nplanes;
     BT ring[PF];
 #pragma unroll
     for (int i = 0; i < PF; i++) {
-        if (i < len) {
+        if (i < len && in_range(ci_ld, cost_blocks)) {
             ring[i] = ld_blk(cost + ci_ld);
         } else {  // zeros, so that lanes without a scanline keep bounded values
 #pragma unroll
@@ -418,10 +420,10 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
 #pragma unroll
         for (int i = 0; i < PF; i++) {
             const BT c = ring[i];
-            ring[i] = ld_blk(cost + ci_ld);
+            if (in_range(ci_ld, cost_blocks)) ring[i] = ld_blk(cost + ci_ld);
             ci_ld += cstep;
             path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv, one, neg256);
-            st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
+            if (in_range(oi, plane_blocks)) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
             oi += ostep;
         }
         rem -= PF;
@@ -430,10 +432,11 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
 #pragma unroll
         for (int i = 0; i < PF; i++) {
             const BT c = ring[i];
-            if (rem > PF) ring[i] = ld_blk(cost + ci_ld);
+            if (rem > PF && in_range(ci_ld, cost_blocks)) ring[i] = ld_blk(cost + ci_ld);
             ci_ld += cstep;
             path_step<LPS, CPL, WIDE, RAGGED>(st, c, P1x2, QPx2, grp, lo_edge, hi_edge, inv, one, neg256);
-            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
+            if (rem > 0 && in_range(oi, plane_blocks))
+                st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
             oi += ostep;
             rem--;
         }
@@ -442,7 +445,8 @@ __device__ __forceinline__ void run_job(const Blk<CPL, WIDE> *__restrict__ cost,
     for (int i = 0; i < PF; i++) {  // the last steps < PF
         if (t0 + i < steps) {
             path_step<LPS, CPL, WIDE, RAGGED>(st, ring[i], P1x2, QPx2, grp, lo_edge, hi_edge, inv, one, neg256);
-            if (rem > 0) st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
+            if (rem > 0 && in_range(oi, plane_blocks))
+                st_blk(planes + oi, pack_plane<CPL, WIDE, RAGGED>(st, inv, c256), pol_stream);
             oi += ostep;
             rem--;
         }
@@ -662,6 +666,8 @@ cudaError_t launch_aggregate_batch(const BatchAggPair *pairs, int npairs, const 
     return launch_k(aggregate_batch_kernel<1, false, prefetch_depth<1, false>()>, dim3(blocks), dim3(kWarps * 32),
                     smem, s, pairs, npairs, prefix, P1x2, P2x2, job_counter);
 }
+
+SGM_GUARD_COUNTER(guard_hits_aggregate)
 
 cudaError_t launch_unpermute(const uint8_t *plane, int W, int H, int D, bool wide, uint16_t *L,
                              cudaStream_t s) {

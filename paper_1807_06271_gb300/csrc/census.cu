@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(kBX *kBY)
         CodeT code;
         if constexpr (sizeof(CodeT) == 8) code = ((uint64_t)hi[r] << 32) | lo[r];
         else code = lo[r];
-        codes[(size_t)blockIdx.z * W * H + (size_t)y * W + x] = code;
+        const long long ci = (long long)blockIdx.z * W * H + (long long)y * W + x;
+        if (in_range(ci, 2LL * W * H)) codes[ci] = code;
     }
 }
 
@@ -135,7 +136,8 @@ __global__ void __launch_bounds__(kBX *kBY)
             code |= (CodeT)(tile_any[(threadIdx.y + wy) * TW + threadIdx.x + wx] < c) << bit;
             bit++;
         }
-    codes[(size_t)blockIdx.z * W * H + (size_t)y * W + x] = code;
+    const long long ci = (long long)blockIdx.z * W * H + (long long)y * W + x;
+    if (in_range(ci, 2LL * W * H)) codes[ci] = code;
 }
 
 // ---------------------------------------------------------------------------
@@ -195,10 +197,11 @@ __global__ void __launch_bounds__(kCostThreads)
     const int xr0 = x0 - Dp - 1;  // right code cr[i] is column xr0 + i
     const CodeT *rowl = codes + (size_t)y * W;
     const CodeT *rowr = codes + (size_t)W * H + (size_t)y * W;
-    for (int i = threadIdx.x; i < kSeg; i += kCostThreads) cl[i] = x0 + i < W ? rowl[x0 + i] : 0;
+    for (int i = threadIdx.x; i < kSeg; i += kCostThreads)
+        cl[i] = x0 + i < W && in_range((long long)y * W + x0 + i, (long long)W * H) ? rowl[x0 + i] : 0;
     for (int i = threadIdx.x; i < kSeg + Dp + 2; i += kCostThreads) {
         const int xr = xr0 + i;
-        cr[i] = (xr >= 0 && xr < W) ? rowr[xr] : 0;
+        cr[i] = (xr >= 0 && xr < W && in_range((long long)W * H + (long long)y * W + xr, 2LL * W * H)) ? rowr[xr] : 0;
     }
     __syncthreads();
     const int chunks = Dp / DPL;
@@ -263,8 +266,11 @@ __global__ void __launch_bounds__(kCostThreads)
     uint8_t *out = cost + ((size_t)y * W + x0) * Dp;
     for (int k = threadIdx.x; k < npx * chunks; k += kCostThreads) {
         const int px = k / chunks, q = k - px * chunks;
-        *reinterpret_cast<VecT *>(out + (size_t)px * Dp + DPL * q) =
-            *reinterpret_cast<const VecT *>(tile + px * stride + DPL * q);
+        // a record of DPL bytes starting at byte o of the W x H x Dp volume
+        const long long o = ((long long)y * W + x0 + px) * Dp + DPL * q;
+        if (in_range(o, (long long)W * H * Dp - DPL + 1))
+            *reinterpret_cast<VecT *>(out + (size_t)px * Dp + DPL * q) =
+                *reinterpret_cast<const VecT *>(tile + px * stride + DPL * q);
     }
 }
 
@@ -292,6 +298,8 @@ cudaError_t launch_census(const uint8_t *left, const uint8_t *right, int pitch, 
     return rect ? launch_k(census_kernel_any<uint64_t, true>, grid, block, smem, s, left, right, pitch, W, H, cw, ch, c, maps)
                 : launch_k(census_kernel_any<uint64_t, false>, grid, block, smem, s, left, right, pitch, W, H, cw, ch, c, maps);
 }
+
+SGM_GUARD_COUNTER(guard_hits_census)
 
 }  // namespace sgm
 

@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(kMX *kMY)
     for (int i = threadIdx.y * kMX + threadIdx.x; i < TW * TH; i += kMX * kMY) {
         const int ty = i / TW, tx = i - ty * TW;
         const int gx = min(max(x0 + tx, 0), W - 1), gy = min(max(y0 + ty, 0), H - 1);
-        tile[ty][tx] = in[(size_t)gy * W + gx];
+        const long long gi = (long long)gy * W + gx;
+        tile[ty][tx] = in_range(gi, (long long)W * H) ? in[gi] : 0xFF;
     }
     __syncthreads();
     const int x = blockIdx.x * kMX + threadIdx.x, y = blockIdx.y * kMY + threadIdx.y;
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kMX *kMY)
     for (int i = 0; i < NP; i++)
         v[i] = i < N ? (uint32_t)tile[threadIdx.y + i / K][threadIdx.x + i % K] : 0x100u;
     OddEvenMergeSort<0, NP>::run(v);
-    out[(size_t)y * W + x] = (uint8_t)v[(N - 1) / 2];
+    if (in_range((long long)y * W + x, (long long)W * H)) out[(size_t)y * W + x] = (uint8_t)v[(N - 1) / 2];
 }
 
 // ---------------------------------------------------------------------------
@@ -96,14 +97,14 @@ __global__ void __launch_bounds__(kUVThreads)
         const int x = x0 + col;
         if (x < W) {
             for (int y = phase; y < H; y += nphase) {
-                const int d = disp[(size_t)y * W + x];
-                if (d < D) atomicAdd(&hist[d * 32 + col], 1u);
+                const int d = in_range((long long)y * W + x, (long long)W * H) ? disp[(size_t)y * W + x] : 0xFF;
+                if (d < D && in_range(d * 32 + col, D * 32)) atomicAdd(&hist[d * 32 + col], 1u);
             }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < D * 32; i += kUVThreads) {
             const int d = i >> 5, c = i & 31;
-            if (x0 + c < W) umap[(size_t)d * W + x0 + c] = (uint16_t)hist[i];
+            if (x0 + c < W && in_range((long long)d * W + x0 + c, (long long)D * W)) umap[(size_t)d * W + x0 + c] = (uint16_t)hist[i];
         }
     } else {
         const int y0 = ((int)blockIdx.x - ustrips) * kVRows;
@@ -112,16 +113,18 @@ __global__ void __launch_bounds__(kUVThreads)
         const int rows = min(kVRows, H - y0);
         for (int i = threadIdx.x; i < rows * W; i += kUVThreads) {
             const int r = i / W, x = i - r * W;
-            const int d = disp[(size_t)(y0 + r) * W + x];
-            if (d < D) atomicAdd(&hist[r * D + d], 1u);
+            const int d = in_range((long long)(y0 + r) * W + x, (long long)W * H) ? disp[(size_t)(y0 + r) * W + x] : 0xFF;
+            if (d < D && in_range(r * D + d, kVRows * D)) atomicAdd(&hist[r * D + d], 1u);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < rows * D; i += kUVThreads)
-            vmap[(size_t)y0 * D + i] = (uint16_t)hist[i];
+            if (in_range((long long)y0 * D + i, (long long)H * D)) vmap[(size_t)y0 * D + i] = (uint16_t)hist[i];
     }
 }
 
 }  // namespace
+
+SGM_GUARD_COUNTER(guard_hits_post)
 
 cudaError_t launch_median(const uint8_t *in, uint8_t *out, int W, int H, int k, cudaStream_t s) {
     dim3 block(kMX, kMY), grid((W + kMX - 1) / kMX, (H + kMY - 1) / kMY);

@@ -670,6 +670,27 @@ int sgm_debug_cost(sgm_handle h, const uint8_t *left, const uint8_t *right, int 
     return rc;
 }
 
+int sgm_debug_guard_hits(unsigned long long *hits, int reset) {
+    if (!hits) return SGM_ERR_INVALID_ARG;
+#ifdef SGM_GUARDED
+    unsigned long long total = 0;
+    for (unsigned long long v : {guard_hits_census(reset != 0), guard_hits_aggregate(reset != 0),
+                                 guard_hits_wta(reset != 0), guard_hits_post(reset != 0)}) {
+        if (v == ~0ull) {
+            cudaGetLastError();
+            return SGM_ERR_CUDA;
+        }
+        total += v;
+    }
+    *hits = total;
+    return SGM_OK;
+#else
+    (void)reset;
+    *hits = 0;
+    return SGM_ERR_UNSUPPORTED;
+#endif
+}
+
 int sgm_debug_stalled_wait(sgm_handle h, const uint8_t *left, const uint8_t *right, void *stream) {
     if (!h || !left || !right) return SGM_ERR_INVALID_ARG;
     if (h->schedule == SGM_SCHEDULE_SWEEP) {

@@ -60,14 +60,52 @@ struct RectMaps {
 
 // Pixel (gx, gy) of the rectified image: the source image read through the
 // maps (Sec. 3.1.1), 0 where a map entry leaves the source.
+// Guarded builds (compiled with -DSGM_GUARDED: a test variant of the
+// library, never the default).  The plane path's kernels (census, the
+// CUDA-core cost, the aggregation, the WTA, the median and the U/V maps)
+// check each global index they compute, and each shared index that depends
+// on the image, against its buffer's extent before the access.  An index out
+// of range skips the access and is counted in the translation unit's
+// counter; sgm_debug_guard_hits sums the counters.  In the default build
+// in_range is constant true and the checks compile away.
+#ifdef SGM_GUARDED
+static __device__ unsigned long long g_guard_hits;  // one per translation unit
+__device__ __forceinline__ bool in_range(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicAdd(&g_guard_hits, 1ull);
+    return false;
+}
+#define SGM_GUARD_COUNTER(name)                                                   \
+    unsigned long long name(bool reset) {                                         \
+        unsigned long long v = 0, z = 0;                                          \
+        if (cudaMemcpyFromSymbol(&v, g_guard_hits, sizeof(v)) != cudaSuccess)     \
+            v = ~0ull;                                                            \
+        if (reset && cudaMemcpyToSymbol(g_guard_hits, &z, sizeof(z)) != cudaSuccess) \
+            v = ~0ull;                                                            \
+        return v;                                                                 \
+    }
+#else
+__device__ __forceinline__ constexpr bool in_range(long long, long long) { return true; }
+#define SGM_GUARD_COUNTER(name) \
+    unsigned long long name(bool) { return 0; }
+#endif
+// Each guarded translation unit's counter (~0 when it cannot be read).
+unsigned long long guard_hits_census(bool reset);
+unsigned long long guard_hits_aggregate(bool reset);
+unsigned long long guard_hits_wta(bool reset);
+unsigned long long guard_hits_post(bool reset);
+
 template <bool RECT>
 __device__ __forceinline__ uint8_t rect_pixel(const uint8_t *__restrict__ img, int pitch, int W,
                                               int H, int gx, int gy, const uint16_t *__restrict__ mx,
                                               const uint16_t *__restrict__ my) {
     if constexpr (!RECT) {
-        return img[(size_t)gy * pitch + gx];
+        const long long i = (long long)gy * pitch + gx;
+        return in_range(i, (long long)pitch * H) ? img[i] : 0;
     } else {
-        const int sx = mx[(size_t)gy * W + gx], sy = my[(size_t)gy * W + gx];
+        const long long m = (long long)gy * W + gx;
+        if (!in_range(m, (long long)W * H)) return 0;
+        const int sx = mx[m], sy = my[m];
         return (sx < W && sy < H) ? img[(size_t)sy * pitch + sx] : 0;
     }
 }

@@ -143,8 +143,8 @@ __device__ __forceinline__ uint32_t pixel_keys(const PlaneChunk<DPL, WIDE> (&v)[
         if (RAGGED && d >= D) key = 0xFFFFFFFFu;
         best = min(best, key);
         if (inside) {
-            if (!RAGGED || d < D) atomicMin(&key_right[x - d], key);
-        } else if (active && x - d >= 0 && (!RAGGED || d < D)) {
+            if ((!RAGGED || d < D) && in_range(x - d, W)) atomicMin(&key_right[x - d], key);
+        } else if (active && x - d >= 0 && (!RAGGED || d < D) && in_range(x - d, W)) {
             atomicMin(&key_right[x - d], key);
         }
         if (DEBUG && active && (!RAGGED || d < D)) dbg_sum[((size_t)y * W + x) * D + d] = (uint16_t)sv;
@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(kThreads, PF == 2 ? 2 : 1)
     const uint8_t *row = planes + (size_t)y * W * rec + DPL * EB * li;
     const uint64_t pol = policy_evict_first();
     const int stride = nwarps * G;
+    // byte offset of a lane's chunk from `planes`, and the last one that fits
+    const long long row_off = (long long)y * W * (long long)rec + DPL * EB * li;
+    const long long chunk_limit = (long long)W * H * (long long)rec - DPL * EB + 1;
     // software pipeline: the planes of the next PF pixel groups are loaded
     // while the current one is reduced (buf[0] is the current group)
     static_assert(PF == 1 || PF == 2, "one or two pixel groups ahead");
@@ -196,17 +199,19 @@ __global__ void __launch_bounds__(kThreads, PF == 2 ? 2 : 1)
     for (int b = 0; b < PF; b++)
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            if ((NP > 0 || q < np) && x + b * stride < W)
+            if ((NP > 0 || q < np) && x + b * stride < W &&
+                in_range(row_off + (long long)(x + b * stride) * (long long)rec + q * Dp * EB, chunk_limit))
                 buf[b][q] = ld_plane<DPL, WIDE>(row + (size_t)(x + b * stride) * rec + q * Dp * EB, pol);
     for (int xb = warp * G; xb < W; xb += stride) {
         const int xn = x + stride, xf = x + PF * stride;
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            if ((NP > 0 || q < np) && xf < W) buf[PF][q] = ld_plane<DPL, WIDE>(row + (size_t)xf * rec + q * Dp * EB, pol);
+            if ((NP > 0 || q < np) && xf < W && in_range(row_off + (long long)xf * (long long)rec + q * Dp * EB, chunk_limit))
+                buf[PF][q] = ld_plane<DPL, WIDE>(row + (size_t)xf * rec + q * Dp * EB, pol);
         const bool active = x < W;
         uint32_t best = pixel_keys<LPS, DPL, WIDE, NP, RAGGED, DEBUG>(buf[0], np, active, x, y, W, D, li, key_right, dbg_sum);
         best = group_min<LPS>(best, lane);
-        if (li == 0 && active) dl_row[x] = (uint8_t)(best & 0xFFu);
+        if (li == 0 && active && in_range(x, W)) dl_row[x] = (uint8_t)(best & 0xFFu);
 #pragma unroll
         for (int b = 0; b < PF; b++)
 #pragma unroll
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, PF == 2 ? 2 : 1)
         uint8_t v = (uint8_t)dl;
         if (tol >= 0) {
             const int xr = xx - dl;
-            if (xr < 0) {
+            if (xr < 0 || !in_range(xr, W)) {
                 v = SGM_INVALID;
             } else {
                 const int dr = (int)(key_right[xr] & 0xFFu);
@@ -228,6 +233,7 @@ __global__ void __launch_bounds__(kThreads, PF == 2 ? 2 : 1)
             }
         }
         const size_t pix = (size_t)y * W + xx;
+        if (!in_range((long long)pix, (long long)W * H)) continue;
         disp_lr[pix] = v;
         if (dbg_left) dbg_left[pix] = (uint8_t)dl;
         if (dbg_right) dbg_right[pix] = (uint8_t)(key_right[xx] & 0xFFu);
@@ -294,6 +300,8 @@ cudaError_t launch_wta_t(const uint8_t *planes, int nplanes, int W, int H, int D
 }
 
 }  // namespace
+
+SGM_GUARD_COUNTER(guard_hits_wta)
 
 cudaError_t launch_wta(const uint8_t *planes, int nplanes, int W, int H, int D, bool wide,
                        int tol, uint8_t *disp_lr, uint8_t *dbg_left, uint8_t *dbg_right,

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "sgm_set_cost_kernel": [_P, _I],
     "sgm_device_status": [_P],
     "sgm_debug_stalled_wait": [_P, _P, _P, _P],
+    "sgm_debug_guard_hits": [ctypes.POINTER(ctypes.c_ulonglong), _I],
     "sgm_debug_fail_alloc": [_I],
     "sgm_debug_canaries": [_I],
     "sgm_debug_check_canaries": [_P],
@@ -133,7 +134,9 @@ SGM_PROBE_POPC_XOR = 2
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libsgm.so, or the build named by SGM_LIBRARY (a test variant of this
+    library such as libsgm_guarded.so; it must exist, nothing falls back)."""
+    return os.environ.get("SGM_LIBRARY") or _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -142,7 +145,7 @@ def load(build_if_missing: bool = True):
     if _lib is not None:
         return _lib
     path = library_path()
-    if build_if_missing and not _build.up_to_date():
+    if build_if_missing and "SGM_LIBRARY" not in os.environ and not _build.up_to_date():
         _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"libsgm.so not found at {path}; build it with "
@@ -502,6 +505,14 @@ def sgm_debug_stalled_wait(h: Handle, left, right, stream=None):
     _check(load().sgm_debug_stalled_wait(
         h.ptr, _dev(left, ("uint8",), shp, "left"), _dev(right, ("uint8",), shp, "right"), _stream(stream)),
         "sgm_debug_stalled_wait")
+
+
+def sgm_debug_guard_hits(reset: bool = False) -> int:
+    """Index-check hits of a guarded build since the last reset (see sgm.h);
+    SgmError(SGM_ERR_UNSUPPORTED) in the default build."""
+    v = ctypes.c_ulonglong()
+    _check(load().sgm_debug_guard_hits(ctypes.byref(v), 1 if reset else 0), "sgm_debug_guard_hits")
+    return v.value
 
 
 def sgm_debug_fail_alloc(n: int):

@@ -269,3 +269,13 @@ def test_batch_entry_points_check_their_arguments_on_the_host():
     D2 = (ctypes.c_int * 2)(64, 64)
     assert lib.sgm_batch_create(2, W, H, D2, ctypes.byref(pitched), ctypes.byref(out)) == sgm.SGM_ERR_INVALID_ARG
     assert out.value is None
+
+
+def test_guard_counter_is_a_guarded_build_feature():
+    """The default library has no index checks: sgm_debug_guard_hits says
+    so without touching the device."""
+    if os.environ.get("SGM_LIBRARY"):
+        pytest.skip("another build of the library is selected")
+    with pytest.raises(sgm.SgmError) as e:
+        sgm.sgm_debug_guard_hits()
+    assert e.value.status == sgm.SGM_ERR_UNSUPPORTED

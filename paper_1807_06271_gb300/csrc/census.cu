@@ -212,9 +212,22 @@ __global__ void __launch_bounds__(kCostThreads)
     // s = px + Dp + 2 - DPL*(i + 1) (even, so the run is 16-byte aligned for
     // 8-byte codes; 2 <= s and s + DPL <= kSeg + Dp): pixel px uses
     // w[DPL - 1 - j], pixel px + 1 uses w[DPL - j].
+    // A thread's pixel pair is the same for all its chunks (kCostThreads is a
+    // multiple of kSeg / 2), so its two left codes are read once.
+    static_assert(kCostThreads % (kSeg / 2) == 0, "one pixel pair per thread");
+    const int px = 2 * (threadIdx.x % (kSeg / 2));
+    CodeT a0, a1;
+    if constexpr (sizeof(CodeT) == 8) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cl + px);
+        a0 = v.x;
+        a1 = v.y;
+    } else {
+        const uint2 v = *reinterpret_cast<const uint2 *>(cl + px);
+        a0 = v.x;
+        a1 = v.y;
+    }
     for (int it = threadIdx.x; it < (kSeg / 2) * chunks; it += kCostThreads) {
-        const int pr = it % (kSeg / 2), i = it / (kSeg / 2);
-        const int px = 2 * pr;
+        const int i = it / (kSeg / 2);
         const int sidx = px + Dp + 2 - DPL * (i + 1);
         CodeT w[DPL + 1];
 #pragma unroll
@@ -230,16 +243,6 @@ __global__ void __launch_bounds__(kCostThreads)
             }
         }
         w[DPL] = cr[sidx + DPL];
-        CodeT a0, a1;
-        if constexpr (sizeof(CodeT) == 8) {
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cl + px);
-            a0 = v.x;
-            a1 = v.y;
-        } else {
-            const uint2 v = *reinterpret_cast<const uint2 *>(cl + px);
-            a0 = v.x;
-            a1 = v.y;
-        }
         uint32_t c[DPL], e[DPL];
 #pragma unroll
         for (int j = 0; j < DPL; j++) {
